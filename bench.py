@@ -1,0 +1,380 @@
+"""Benchmark of the fused feature-extraction path on a 4-band 16384^2 uint16 scene.
+
+A step is one pass of the whole path (LoG x2, zero crossings, contrast,
+standard deviation, OR, hybrid median) over the 4 bands of a synthetic
+multispectral scene (12-bit values, band by band, one fused launch per band).
+Inputs are resident in HBM and larger than L2 (512 MiB per band).
+
+Prints one JSON line.  Keys beyond the driver contract:
+  roofline    the fused kernel against the measured HBM copy bandwidth
+  issue_roof  the same kernel against the SM issue rate (lane-instructions)
+  batched     64 uneven scenes (uint8/uint16 mixed) in one persistent
+              graph-replayed launch versus 64 plain launches
+  cpu_baseline  the FP64 oracle on the host cores, on a bounded row sample
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import concurrent.futures as cf
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+SIDE = 16384
+BANDS = 4
+BYTES_PER_PX = 3  # one uint16 read + one uint8 mask write (algorithmic)
+WORKLOAD = "4-band multispectral 16384x16384 uint16 (12-bit), band by band"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="fx", choices=["fx", "reference"])
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched-vs-plain comparison")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--side", type=int, default=SIDE, help="band side (default 16384)")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------ CPU oracle
+
+def oracle_sample(band: np.ndarray, rows: int, threads: int) -> dict:
+    """The FP64 oracle as it stands on `rows` rows of one band, split in row
+    chunks over `threads` host threads (each chunk carries its own halo)."""
+    import oracle
+    oracle.build()
+    p = oracle.default_params(16.0)
+    y0 = (band.shape[0] - rows) // 2
+    chunk = max(16, rows // (threads * 2))
+    spans = [(y, min(y + chunk, y0 + rows)) for y in range(y0, y0 + rows, chunk)]
+    t = time.perf_counter()
+    with cf.ThreadPoolExecutor(max_workers=threads) as ex:
+        list(ex.map(lambda s: oracle.extract(band, p, rows=s), spans))
+    dt = time.perf_counter() - t
+    px = rows * band.shape[1]
+    return {"px": px, "seconds": dt, "gpx_s": px / dt / 1e9}
+
+
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+# ---------------------------------------------------------------- clocks
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self._t = threading.Thread(target=self._read, daemon=True)
+            self._t.start()
+            time.sleep(0.3)
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            time.sleep(0.15)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self) -> dict:
+        sm, mx, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) != 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[3:]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------- profiles
+
+def kernel_source_sha() -> str:
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_1304_3992_gb300", "csrc")
+    for n in sorted(os.listdir(d)):
+        if n.endswith((".cu", ".cuh", ".h", ".cpp")):
+            h.update(open(os.path.join(d, n), "rb").read())
+    return h.hexdigest()
+
+
+def profiled_traffic(kernel_key: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on
+    the current kernel sources (else None)."""
+    path = os.path.join(ROOT, "profiles", f"{kernel_key}.txt")
+    if not os.path.exists(path):
+        return None
+    kv = {}
+    for line in open(path):
+        if ":" in line and not line.startswith("#"):
+            k, v = line.split(":", 1)
+            kv[k.strip()] = v.strip()
+    if kv.get("source_sha256") != kernel_source_sha():
+        return None
+    try:
+        return float(kv["dram_bytes_per_launch_full_size"])
+    except (KeyError, ValueError):
+        return None
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured", d
+    return 6800.0, "fallback", {}
+
+
+# ----------------------------------------------------------- reference arm
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from gen import scenes
+    band = next(scenes.ms_bands_u16_12bit(side=args.side, bands=[0]))
+    cores = host_cores()
+    rows = 128
+    times = []
+    for i in range(args.warmup + args.steps):
+        r = oracle_sample(band, rows, cores)
+        if i >= args.warmup:
+            times.append(r["seconds"])
+    px = rows * band.shape[1]
+    v = px * len(times) / sum(times) / 1e9
+    line = {
+        "impl": "reference", "metric": "fused extraction throughput", "value": v, "unit": "Gpixel/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "side": args.side, "bands": BANDS,
+                   "sample": f"{rows} rows x {band.shape[1]} px of band 0 per step"},
+        "cpu_baseline": {"value": v, "unit": "Gpixel/s", "cores": cores, "kind": "oracle",
+                         "sample": f"{rows} rows x {band.shape[1]} px of band 0 per step, row chunks over {cores} threads"},
+        "e2e": {"value": v, "unit": "Gpixel/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ main
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from gen import scenes
+    from paper_1304_3992_gb300 import fx
+
+    # ---- workload: 4 bands resident in HBM
+    bands_np = list(scenes.ms_bands_u16_12bit(side=args.side))
+    bands = [torch.from_numpy(b).to(dev) for b in bands_np]
+    outs = [torch.empty(b.shape, dtype=torch.uint8, device=dev) for b in bands]
+    params = fx.make_params(fx.FX_U16, 12)
+    stream = torch.cuda.current_stream()
+    px_step = sum(b.numel() for b in bands)
+
+    def step(ev=None):
+        for i, (b, o) in enumerate(zip(bands, outs)):
+            if ev is not None:
+                ev[2 * i].record(stream)
+            fx.extract(b, params, out=o, stream=stream)
+            if ev is not None:
+                ev[2 * i + 1].record(stream)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+
+    K = args.steps
+    launch_ev = [[torch.cuda.Event(enable_timing=True) for _ in range(2 * BANDS)] for _ in range(K)]
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clocks:
+        barrier()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for k in range(K):
+            step(launch_ev[k])
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+    elapsed_ms = e0.elapsed_time(e1)
+    launch_ms = [launch_ev[k][2 * i].elapsed_time(launch_ev[k][2 * i + 1]) for k in range(K) for i in range(BANDS)]
+    if world > 1:
+        t = torch.tensor([elapsed_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+    value = world * px_step * K / (elapsed_ms * 1e-3) / 1e9
+
+    # ---- end to end through the C ABI on pinned host buffers
+    h_in = [torch.from_numpy(b).pin_memory() for b in bands_np]
+    h_out = [torch.empty(b.shape, dtype=torch.uint8).pin_memory() for b in bands_np]
+    plan = fx.Plan(params, max_images=BANDS, device=local)
+    for i in range(BANDS):  # warm-up: grows the staging buffers
+        plan.extract_host(h_in[i].numpy(), h_out[i].numpy())
+    ke = max(1, min(K, 5))
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(ke):
+        for i in range(BANDS):
+            plan.extract_host(h_in[i].numpy(), h_out[i].numpy())
+    e2e_s = time.perf_counter() - t0
+    barrier()
+    e2e_ok = all(torch.equal(h_out[i].to(dev), outs[i]) for i in range(BANDS))
+    e2e = {"value": world * px_step * ke / e2e_s / 1e9, "unit": "Gpixel/s",
+           "h2d_bytes_per_step": sum(b.nbytes for b in bands_np),
+           "d2h_bytes_per_step": sum(b.size for b in bands_np), "matches_device_path": bool(e2e_ok)}
+
+    # ---- batched persistent launch vs 64 plain launches (uneven scenes)
+    batched = None
+    if not args.no_batch:
+        batched = bench_batched(fx, torch, dev, params, plan_cls=fx.Plan)
+    plan.close()
+
+    # ---- roofline of the fused kernel
+    peak, peak_src, _ = peaks()
+    avg_launch_ms = sum(launch_ms) / len(launch_ms)
+    px_launch = bands[0].numel()
+    achieved = BYTES_PER_PX * px_launch / (avg_launch_ms * 1e-3) / 1e9
+    traffic = profiled_traffic("fused_extract_16384_u16")
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": traffic, "algorithmic_bytes_per_launch": BYTES_PER_PX * px_launch,
+            "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs copy)" if peak_src == "measured" else peak_src,
+            "kernel_ms": avg_launch_ms}
+    props = torch.cuda.get_device_properties(dev)
+    clk = clocks.summary()
+    mhz = clk["sm_mhz"] or 1900.0
+    issue_peak = props.multi_processor_count * 128 * mhz * 1e6  # lane-instructions/s
+    issue = {"sm_count": props.multi_processor_count, "sm_mhz": mhz,
+             "peak_lane_inst_per_s": issue_peak,
+             "lane_inst_per_px_at_roof": issue_peak / (px_launch / (avg_launch_ms * 1e-3))}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        cores = host_cores()
+        r = oracle_sample(bands_np[0], 1024, cores)
+        cpu = {"value": r["gpx_s"], "unit": "Gpixel/s", "cores": cores, "kind": "oracle",
+               "sample": f"1024 rows x {args.side} px of band 0 ({r['px']} px, {r['seconds']:.1f} s wall), "
+                         f"row chunks over {cores} threads"}
+
+    if rank == 0:
+        line = {
+            "metric": "fused extraction throughput", "value": value, "unit": "Gpixel/s", "n_gpus": world,
+            "steps": K, "warmup": max(3, args.warmup), "ms_per_step": elapsed_ms / K,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "side": args.side, "bands": BANDS, "values": "12-bit",
+                       "launch": "fx_extract per band (one fused kernel each)",
+                       "parallelism": f"replicas x{world}", "l2": "inputs larger than L2 (512 MiB per band)"},
+            "roofline": roof, "issue_roof": issue, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": K * BANDS, "clocks": clk, "batched": batched,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def bench_batched(fx, torch, dev, params, plan_cls):
+    from gen import scenes
+    batch = scenes.uneven_batch(n=64)
+    imgs, outs = [], []
+    for view, buf in batch:
+        t = torch.from_numpy(buf).to(dev)
+        imgs.append(t[:, :view.shape[1]])
+        outs.append(torch.empty(view.shape, dtype=torch.uint8, device=dev))
+    pairs = list(zip(imgs, outs))
+    px = sum(o.numel() for o in outs)
+    stream = torch.cuda.current_stream()
+    plan = plan_cls(params, max_images=64, device=dev.index or 0)
+    tuned = plan.autotune(pairs)
+
+    def time_it(fn, reps=5):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        best = 1e30
+        for _ in range(reps):
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1))
+        return best
+
+    t_batch = time_it(lambda: plan.extract_batch(pairs))
+    ref = [o.clone() for o in outs]
+    t_plain = time_it(lambda: [fx.extract(i, params, out=o) for i, o in pairs])
+    same = all(torch.equal(a, b) for a, b in zip(ref, outs))
+    plan.close()
+    return {"scenes": 64, "pixels": px, "batched_gpx_s": px / t_batch / 1e6,
+            "one_by_one_gpx_s": px / t_plain / 1e6, "speedup": t_plain / t_batch,
+            "identical_output": bool(same), "tile": list(tuned)}
+
+
+if __name__ == "__main__":
+    main()

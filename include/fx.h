@@ -1,0 +1,202 @@
+/*
+ * fx.h -- C ABI of the GB300 feature-extraction library (libfx.so).
+ *
+ * The library computes, on one NVIDIA GB300 (sm_103a), the data-parallel
+ * feature-extraction path of "GPU Accelerated Automated Feature Extraction
+ * from Satellite Images" (arXiv 1304.3992): for every pixel of a single-band
+ * uint8/uint16 image
+ *   1. two 5x5 Laplacian-of-Gaussian responses L1, L2 (Sec. 3.1, Eq. 1,
+ *      sigma 0.5 and 20 per Sec. 4.1);
+ *   2. zero crossings of each response among the 4 neighbours, kept when the
+ *      positive maximum minus the negative minimum exceeds a threshold
+ *      (Sec. 3.2, Sec. 4);
+ *   3. the local standard-deviation test (Eq. 2): 5x5 window, re-computed on
+ *      the 3x3 window above a maximum threshold (Sec. 4.1);
+ *   4. OR-combination of the two extracted maps (Sec. 4.1);
+ *   5. an optional hybrid median filter (Sec. 3.4), optionally repeated with
+ *      several window sizes (Sec. 4, Sec. 4.2).
+ * The output is a binary mask, one uint8 (0 or 1) per pixel.
+ *
+ * Readings where the paper is silent (the masks are the zero-sum integer
+ * rounding of Eq. 1 scaled to max |w| = mask_q; every stage extends past the
+ * image border by replication; zero-crossing ties go to the negative pixel;
+ * s > T is decided exactly as Lambda*sum(a^2) - (sum a)^2 > T^2 Lambda
+ * (Lambda-1); the combination is OR) are fixed here and documented per field.
+ *
+ * Conventions for every entry point:
+ *   - All image and mask pointers are DEVICE pointers unless the name says
+ *     _host.  The caller owns them; the library never frees them and keeps no
+ *     reference after the call returns.
+ *   - Work is enqueued on `stream` (a cudaStream_t; NULL = legacy default
+ *     stream) and runs asynchronously; the returned status reports host-side
+ *     validation and launch errors only.
+ *   - On any error nothing is launched and no output byte is written.
+ *   - No call throws; no call prints.
+ *   - Results are bit-identical to the definition above for every input
+ *     value: integer masks, exact integer/FP32-exact arithmetic.
+ */
+#ifndef FX_H
+#define FX_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  FX_OK = 0,
+  FX_ERR_INVALID_ARG = 1, /* null pointer, bad size/pitch/alignment/dtype, NaN parameter */
+  FX_ERR_UNSUPPORTED = 2, /* valid request outside what the library implements */
+  FX_ERR_RANGE = 3,       /* parameters whose exact evaluation would overflow 32-bit sums */
+  FX_ERR_CUDA = 4,        /* a CUDA runtime call or a launch failed */
+  FX_ERR_NOMEM = 5,       /* a device or pinned-host allocation failed */
+  FX_ERR_BUDGET = 6,      /* request larger than a configured memory budget */
+  FX_ERR_TIMEOUT = 7      /* a bounded device-side wait gave up */
+} fx_status;
+
+typedef enum { FX_U8 = 1, FX_U16 = 2 } fx_dtype;
+
+#define FX_MAX_HMF_LEVELS 4
+
+typedef struct {
+  /* sizeof(fx_params); set by fx_params_default, checked by every call. */
+  uint32_t struct_size;
+  /* Gaussian sigma of the two LoG masks (Eq. 1; Sec. 4.1 uses 0.5 and 20). */
+  double sigma[2];
+  /* Integer mask scale Q: the mean-removed Eq. 1 samples are scaled to
+   * max |w| = Q, rounded half away from zero, and the centre tap is reset to
+   * minus the sum of the other 24 (zero-sum).  Default 512. */
+  int32_t mask_q;
+  /* Zero-crossing contrast thresholds per branch, in response units:
+   * keep a crossing when max - min of L over it and its 4 neighbours > t_zc. */
+  double t_zc[2];
+  /* Standard-deviation thresholds per branch, in image units (Eq. 2):
+   * S = (s5 > t_sdmax) ? (s3 > t_sd3) : (s5 > t_sd5).  A negative threshold
+   * always passes. */
+  double t_sd5[2], t_sdmax[2], t_sd3[2];
+  /* 0 = the standard deviation is taken over the image (default); 1 = over
+   * the binary zero-crossing map of the same branch (Sec. 4.1 literal). */
+  int32_t stddev_source;
+  /* Hybrid-median windows applied in order (3 or 5; 0 ends the list).
+   * Default {5, 0, 0, 0}; all zero switches the filter off. */
+  int32_t hmf[FX_MAX_HMF_LEVELS];
+  /* Nominal radiometric depth used only to scale the default thresholds
+   * (value scale 2^(bits-8)); it never restricts the input values. */
+  int32_t bits;
+  /* Row pitch of out_mask in bytes for fx_extract; 0 = width. */
+  int64_t out_pitch;
+} fx_params;
+
+/*
+ * Fill *p with the defaults: sigma {0.5, 20}, mask_q 512, hmf {5}, image
+ * stddev source, and thresholds for a 12-DN step on 8-bit data times the
+ * value scale s = 2^(bits-8): t_zc = {4248 s, 15360 s}, t_sd5 = t_sd3 = 6 s,
+ * t_sdmax = 24 s.  bits = 0 selects 8 for FX_U8 and 12 for FX_U16 (the
+ * 12-bit radiometry of the paper's AWiFS scenes, Sec. 6).  p may not be NULL.
+ */
+void fx_params_default(fx_params *p, fx_dtype dtype, int32_t bits);
+
+/*
+ * The integer mask of one branch (reading of Eq. 1 above) into w[25]
+ * (row-major, w[(dy+2)*5 + dx+2]).  Returns FX_ERR_INVALID_ARG for sigma <= 0,
+ * mask_q < 1 or non-finite values.
+ */
+fx_status fx_log_mask(double sigma, int32_t mask_q, int32_t w[25]);
+
+/*
+ * One image, stateless (Sec. 4.1 flow, one fused kernel launch).
+ *   img          device pointer to row 0; aligned to the element size
+ *   width,height pixels, both >= 1
+ *   pitch_bytes  distance between image rows, >= width*elem, multiple of elem
+ *   dtype        FX_U8 or FX_U16
+ *   params       NULL = fx_params_default(dtype, 0)
+ *   out_mask     device pointer, height rows of params->out_pitch (or width)
+ *                bytes; must not overlap the image
+ * Errors: FX_ERR_INVALID_ARG, FX_ERR_RANGE, FX_ERR_UNSUPPORTED, FX_ERR_CUDA.
+ * Thread-safe; allocates nothing.
+ */
+fx_status fx_extract(const void *img, int64_t width, int64_t height, int64_t pitch_bytes,
+                     fx_dtype dtype, const fx_params *params, uint8_t *out_mask, void *stream);
+
+/* ------------------------------------------------------------------ plans */
+
+typedef struct fx_plan fx_plan;
+
+/*
+ * A plan fixes the parameters and owns the device workspace of the batched
+ * path: descriptor table, tile-queue counter, device status word, cached CUDA
+ * graph and the tuned tile configuration.  One host thread uses a plan at a
+ * time.  max_images bounds fx_extract_batch's n (>= 1).  device is the CUDA
+ * device ordinal the workspace lives on.
+ * Errors: FX_ERR_INVALID_ARG, FX_ERR_RANGE, FX_ERR_NOMEM, FX_ERR_CUDA.
+ */
+fx_status fx_plan_create(fx_plan **plan, const fx_params *params, int32_t max_images,
+                         int32_t device);
+
+/* Releases the plan's workspace after waiting for its outstanding work. */
+fx_status fx_plan_destroy(fx_plan *plan);
+
+typedef struct {
+  const void *img;     /* device pointer to row 0 of the image */
+  int64_t width, height, pitch_bytes;
+  int32_t dtype;       /* fx_dtype */
+  int32_t reserved;
+  uint8_t *out_mask;   /* device pointer */
+  int64_t out_pitch;   /* bytes; 0 = width */
+} fx_image_desc;
+
+/*
+ * Many images of uneven sizes and mixed dtypes in ONE persistent launch over
+ * a tile queue, replayed from a CUDA graph (the batched form of Sec. 6.2.2's
+ * one-thread-per-pixel mapping).  Each image's mask is byte-identical to
+ * fx_extract's.  descs is a HOST array of n descriptors, validated like
+ * fx_extract's arguments; the table is copied before the call returns.
+ * Output masks must not overlap each other or any input.
+ * Errors: FX_ERR_INVALID_ARG (n < 1, n > max_images, bad descriptor),
+ * FX_ERR_CUDA.
+ */
+fx_status fx_extract_batch(fx_plan *plan, const fx_image_desc *descs, int32_t n, void *stream);
+
+/*
+ * Tile configuration of the batched kernel: tile width/height in pixels and
+ * CTAs per SM.  fx_plan_autotune times the candidates on the given images
+ * (outputs are overwritten) and keeps the fastest; fx_plan_set_tile forces one
+ * (tile_w in {32, 64, 128}, tile_h in {8, 16, 32, 64}, ctas_per_sm in 1..8).
+ */
+fx_status fx_plan_autotune(fx_plan *plan, const fx_image_desc *descs, int32_t n, void *stream,
+                           int32_t *tile_w, int32_t *tile_h, int32_t *ctas_per_sm);
+fx_status fx_plan_set_tile(fx_plan *plan, int32_t tile_w, int32_t tile_h, int32_t ctas_per_sm);
+
+/*
+ * Synchronises `stream` and reads the plan's device status word, which the
+ * batched kernel sets when a descriptor fails its device-side check or a
+ * bounded wait gives up; the word is cleared by the read.
+ */
+fx_status fx_get_device_status(fx_plan *plan, void *stream);
+
+/*
+ * End-to-end call on HOST buffers: copies the image to the device in row
+ * bands, extracts, and copies the mask back, overlapping the copies of one
+ * band with the kernel of the previous one on the plan's own streams.  Host
+ * buffers should be page-locked for full copy speed.  Synchronous: the mask
+ * is in out_mask_host when the call returns.  The plan grows its staging
+ * buffers on first use.
+ * Errors: as fx_extract, plus FX_ERR_NOMEM.
+ */
+fx_status fx_extract_host(fx_plan *plan, const void *img_host, int64_t width, int64_t height,
+                          int64_t pitch_bytes, fx_dtype dtype, uint8_t *out_mask_host,
+                          int64_t out_pitch);
+
+/* Human-readable name of a status code (static storage). */
+const char *fx_status_string(fx_status s);
+
+/* Library version, e.g. "fx 1.0 sm_103a". */
+const char *fx_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FX_H */

@@ -1,0 +1,57 @@
+// fx_internal.h -- types shared by the host side of libfx and its kernels.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/fx.h"
+
+namespace fx {
+
+// Per-call constants of the method, derived on the host from fx_params.
+struct KParams {
+  // Integer LoG masks (Eq. 1 reading), row-major 5x5, and their 6 ring values
+  // for squared radii 0, 1, 2, 4, 5, 8 (the masks are radial, hence D4-symmetric).
+  int32_t w[2][25];
+  int32_t ring[2][6];
+  float ringf[2][6];
+  // Contrast test max - min > t_zc  <=>  max - min > tzc (integers).
+  int32_t tzc[2];
+  // Standard-deviation tests s > T  <=>  D > t with D = Lambda*sum(a^2) - (sum a)^2
+  // and t = floor(T^2 Lambda (Lambda-1)) (-1 when T < 0, i.e. always true).
+  int64_t tsd5[2], tsdmax[2], tsd3[2];
+  int32_t source;  // 0 = image, 1 = binary zero-crossing map
+  int32_t nhmf;    // number of hybrid-median passes
+  int32_t hmf[FX_MAX_HMF_LEVELS];
+  int32_t r_m;     // total radius of the median passes
+  int32_t r_in;    // input radius of one output pixel
+  // Largest sum of positive taps over both masks; bounds |L| <= maxval * splus.
+  int64_t splus;
+};
+
+// Derive KParams from fx_params for images whose values are <= maxval.
+fx_status make_kparams(const fx_params *p, int32_t maxval, KParams *kp);
+
+// Validation shared by fx_extract and the descriptors of fx_extract_batch.
+fx_status check_image(const void *img, int64_t width, int64_t height, int64_t pitch_bytes,
+                      int32_t dtype, const uint8_t *out, int64_t out_pitch);
+
+// Launchers (fx_tile.cu, fx_stream.cu).  Row window: output rows [y_begin, y_end)
+// of an image of height `height`; `img` points at image row `row0` (the buffer
+// holds rows [row0, ...)), `out` at output row y_begin.
+struct ImageView {
+  const void *img;
+  int64_t width, height, pitch;  // pitch in bytes
+  int64_t row0;
+  int32_t elem;                  // 1 or 2
+  uint8_t *out;
+  int64_t out_pitch;
+  int64_t y_begin, y_end;
+};
+
+cudaError_t launch_tile_general(const ImageView &v, const KParams &kp, cudaStream_t s);
+bool fast_path_supported(const KParams &kp);
+cudaError_t launch_fast(const ImageView &v, const KParams &kp, cudaStream_t s);
+cudaError_t launch_extract(const ImageView &v, const KParams &kp, cudaStream_t s);
+
+}  // namespace fx

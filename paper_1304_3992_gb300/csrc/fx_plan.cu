@@ -1,0 +1,470 @@
+// fx_plan.cu -- plans: the batched persistent kernel over a tile queue (CUDA
+// graph replay), its tile-configuration tuner, the device status word, and the
+// end-to-end entry point on host buffers.
+#include <algorithm>
+#include <cstdint>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "fx_internal.h"
+#include "fx_stream.cuh"
+#include "fx_tile.cuh"
+
+namespace fx {
+namespace {
+
+struct BatchImage {
+  const void *img;
+  int64_t width, height, pitch;
+  uint8_t *out;
+  int64_t out_pitch;
+  int64_t units_x;     // work units across the image
+  int64_t unit_begin;  // first queue index of this image
+  int32_t elem;
+  int32_t pad;
+};
+
+struct BatchHeader {
+  int64_t total_units;
+  int32_t n;
+  int32_t unit_w, unit_h;  // unit shape in output pixels
+  int32_t pad;
+};
+
+size_t table_bytes(int max_images) { return sizeof(BatchHeader) + sizeof(BatchImage) * max_images; }
+
+// Status bits written by the batch kernel.
+constexpr int kStatusBadDescriptor = 1;
+
+// Persistent kernel: CTAs pop work units (one output tile / strip segment of
+// one image) from a global counter until the queue is empty.  Units of
+// different images and dtypes interleave freely.
+template <bool kFast>
+__global__ void __launch_bounds__(256) batch_kernel(const unsigned char *table,
+                                                    unsigned long long *counter, int *status,
+                                                    KParams kp8, KParams kp16) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ long long s_unit;
+  const BatchHeader *hdr = reinterpret_cast<const BatchHeader *>(table);
+  const BatchImage *ims = reinterpret_cast<const BatchImage *>(table + sizeof(BatchHeader));
+  const long long total = hdr->total_units;
+  const int n = hdr->n;
+  for (;;) {
+    if (threadIdx.x == 0) s_unit = static_cast<long long>(atomicAdd(counter, 1ULL));
+    __syncthreads();
+    const long long u = s_unit;
+    __syncthreads();
+    if (u >= total) break;
+    int lo = 0, hi = n - 1;  // last image whose first unit is <= u
+    while (lo < hi) {
+      int mid = (lo + hi + 1) >> 1;
+      if (ims[mid].unit_begin <= u) lo = mid;
+      else hi = mid - 1;
+    }
+    const BatchImage &b = ims[lo];
+    const long long local = u - b.unit_begin;
+    if (b.units_x <= 0 || (b.elem != 1 && b.elem != 2)) {
+      if (threadIdx.x == 0) atomicOr(status, kStatusBadDescriptor);
+      continue;
+    }
+    ImageView v{b.img, b.width, b.height, b.pitch, 0, b.elem, b.out, b.out_pitch, 0, b.height};
+    const int64_t ux = local % b.units_x, uy = local / b.units_x;
+    if constexpr (kFast) {
+      if (b.elem == 1) fast_unit<uint8_t>(v, kp8, ux, uy, hdr->unit_w, hdr->unit_h, smem);
+      else fast_unit<uint16_t>(v, kp16, ux, uy, hdr->unit_w, hdr->unit_h, smem);
+    } else {
+      if (b.elem == 1) gen::general_tile<uint8_t>(v, kp8, ux * gen::TW, uy * gen::TH, smem);
+      else gen::general_tile<uint16_t>(v, kp16, ux * gen::TW, uy * gen::TH, smem);
+    }
+    __syncthreads();
+  }
+}
+
+}  // namespace
+}  // namespace fx
+
+using namespace fx;
+
+struct fx_plan {
+  fx_params params;
+  KParams kp8, kp16;
+  fx_status st16;  // FX_ERR_RANGE when 16-bit images cannot be evaluated exactly
+  bool fast;
+  int device, max_images, num_sms;
+  // batch workspace
+  unsigned char *d_table;
+  unsigned char *h_table[2];
+  cudaEvent_t h_free[2];
+  int h_next;
+  unsigned long long *d_counter;
+  int *d_status;
+  cudaGraphExec_t graph[2];
+  int unit_w, unit_h, ctas_per_sm;
+  size_t smem;
+  // end-to-end path on host buffers
+  cudaStream_t s_h2d, s_comp, s_d2h;
+  void *d_in[2];
+  uint8_t *d_out[2];
+  size_t in_cap, out_cap;
+  cudaEvent_t ev_in[2], ev_comp[2], ev_out[2];
+};
+
+namespace {
+
+void destroy_graphs(fx_plan *p) {
+  for (int i = 0; i < 2; ++i)
+    if (p->graph[i]) {
+      cudaGraphExecDestroy(p->graph[i]);
+      p->graph[i] = nullptr;
+    }
+}
+
+size_t unit_smem(const fx_plan *p) {
+  if (p->fast) return fast_smem_bytes(std::max(p->kp8.r_in, p->kp16.r_in), p->unit_w, p->unit_h);
+  return std::max(gen::general_smem_bytes(p->kp8), gen::general_smem_bytes(p->kp16));
+}
+
+// Graph i: copy host table i to the device, zero the queue counter, run the
+// persistent kernel.  The table copy has a fixed size so the graph never changes.
+fx_status build_graph(fx_plan *p, int i) {
+  p->smem = unit_smem(p);
+  const void *fn = p->fast ? reinterpret_cast<const void *>(&batch_kernel<true>)
+                           : reinterpret_cast<const void *>(&batch_kernel<false>);
+  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) != cudaSuccess)
+    return FX_ERR_CUDA;
+  cudaGraph_t g;
+  if (cudaGraphCreate(&g, 0) != cudaSuccess) return FX_ERR_CUDA;
+  cudaGraphNode_t n_copy, n_zero, n_kern;
+  cudaMemcpy3DParms cp;
+  std::memset(&cp, 0, sizeof cp);
+  cp.srcPtr = make_cudaPitchedPtr(p->h_table[i], table_bytes(p->max_images), table_bytes(p->max_images), 1);
+  cp.dstPtr = make_cudaPitchedPtr(p->d_table, table_bytes(p->max_images), table_bytes(p->max_images), 1);
+  cp.extent = make_cudaExtent(table_bytes(p->max_images), 1, 1);
+  cp.kind = cudaMemcpyHostToDevice;
+  cudaMemsetParams ms;
+  std::memset(&ms, 0, sizeof ms);
+  ms.dst = p->d_counter;
+  ms.value = 0;
+  ms.elementSize = 4;
+  ms.width = 2;
+  ms.height = 1;
+  ms.pitch = 8;
+  const unsigned char *tab = p->d_table;
+  unsigned long long *ctr = p->d_counter;
+  int *stp = p->d_status;
+  KParams k8 = p->kp8, k16 = p->kp16;
+  void *args[] = {&tab, &ctr, &stp, &k8, &k16};
+  cudaKernelNodeParams kn;
+  std::memset(&kn, 0, sizeof kn);
+  kn.func = const_cast<void *>(fn);
+  kn.gridDim = dim3(static_cast<unsigned>(p->num_sms * p->ctas_per_sm));
+  kn.blockDim = dim3(256);
+  kn.sharedMemBytes = static_cast<unsigned>(p->smem);
+  kn.kernelParams = args;
+  cudaError_t e = cudaGraphAddMemcpyNode(&n_copy, g, nullptr, 0, &cp);
+  if (e == cudaSuccess) e = cudaGraphAddMemsetNode(&n_zero, g, &n_copy, 1, &ms);
+  if (e == cudaSuccess) e = cudaGraphAddKernelNode(&n_kern, g, &n_zero, 1, &kn);
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&p->graph[i], g, 0);
+  cudaGraphDestroy(g);
+  return e == cudaSuccess ? FX_OK : FX_ERR_CUDA;
+}
+
+fx_status rebuild(fx_plan *p) {
+  destroy_graphs(p);
+  for (int i = 0; i < 2; ++i) {
+    fx_status st = build_graph(p, i);
+    if (st != FX_OK) return st;
+  }
+  return FX_OK;
+}
+
+fx_status fill_table(fx_plan *p, unsigned char *h, const fx_image_desc *d, int32_t n) {
+  BatchHeader *hdr = reinterpret_cast<BatchHeader *>(h);
+  BatchImage *ims = reinterpret_cast<BatchImage *>(h + sizeof(BatchHeader));
+  const int uw = p->fast ? p->unit_w : gen::TW, uh = p->fast ? p->unit_h : gen::TH;
+  int64_t total = 0;
+  for (int32_t i = 0; i < n; ++i) {
+    const int64_t op = d[i].out_pitch ? d[i].out_pitch : d[i].width;
+    fx_status st = check_image(d[i].img, d[i].width, d[i].height, d[i].pitch_bytes, d[i].dtype,
+                               d[i].out_mask, op);
+    if (st != FX_OK) return st;
+    if (d[i].dtype == FX_U16 && p->st16 != FX_OK) return p->st16;
+    BatchImage &b = ims[i];
+    b.img = d[i].img;
+    b.width = d[i].width;
+    b.height = d[i].height;
+    b.pitch = d[i].pitch_bytes;
+    b.out = d[i].out_mask;
+    b.out_pitch = op;
+    b.elem = d[i].dtype == FX_U8 ? 1 : 2;
+    b.pad = 0;
+    b.units_x = (b.width + uw - 1) / uw;
+    b.unit_begin = total;
+    total += b.units_x * ((b.height + uh - 1) / uh);
+  }
+  // outputs must not overlap each other (inputs were checked per descriptor)
+  for (int32_t i = 0; i < n; ++i)
+    for (int32_t j = i + 1; j < n; ++j) {
+      uintptr_t a0 = reinterpret_cast<uintptr_t>(ims[i].out), a1 = a0 + (ims[i].height - 1) * ims[i].out_pitch + ims[i].width;
+      uintptr_t b0 = reinterpret_cast<uintptr_t>(ims[j].out), b1 = b0 + (ims[j].height - 1) * ims[j].out_pitch + ims[j].width;
+      uintptr_t c0 = reinterpret_cast<uintptr_t>(ims[j].img), c1 = c0 + (ims[j].height - 1) * ims[j].pitch + ims[j].width * ims[j].elem;
+      uintptr_t e0 = reinterpret_cast<uintptr_t>(ims[i].img), e1 = e0 + (ims[i].height - 1) * ims[i].pitch + ims[i].width * ims[i].elem;
+      if ((a0 < b1 && b0 < a1) || (a0 < c1 && c0 < a1) || (b0 < e1 && e0 < b1)) return FX_ERR_INVALID_ARG;
+    }
+  hdr->total_units = total;
+  hdr->n = n;
+  hdr->unit_w = uw;
+  hdr->unit_h = uh;
+  hdr->pad = 0;
+  return FX_OK;
+}
+
+void free_host_path(fx_plan *p) {
+  for (int i = 0; i < 2; ++i) {
+    if (p->d_in[i]) cudaFree(p->d_in[i]);
+    if (p->d_out[i]) cudaFree(p->d_out[i]);
+    p->d_in[i] = nullptr;
+    p->d_out[i] = nullptr;
+  }
+  p->in_cap = p->out_cap = 0;
+}
+
+}  // namespace
+
+extern "C" {
+
+fx_status fx_plan_create(fx_plan **out, const fx_params *params, int32_t max_images, int32_t device) {
+  if (!out || max_images < 1 || max_images > (1 << 20)) return FX_ERR_INVALID_ARG;
+  *out = nullptr;
+  fx_params def;
+  if (!params) {
+    fx_params_default(&def, FX_U16, 0);
+    params = &def;
+  }
+  if (params->struct_size != sizeof(fx_params)) return FX_ERR_INVALID_ARG;
+  fx_plan *p = new (std::nothrow) fx_plan;
+  if (!p) return FX_ERR_NOMEM;
+  std::memset(static_cast<void *>(p), 0, sizeof(*p));
+  p->params = *params;
+  fx_status st = make_kparams(params, 255, &p->kp8);
+  if (st != FX_OK) {
+    delete p;
+    return st;
+  }
+  p->st16 = make_kparams(params, 65535, &p->kp16);
+  if (p->st16 != FX_OK) p->kp16 = p->kp8;
+  p->fast = fast_path_supported(p->kp8) && fast_path_supported(p->kp16);
+  p->device = device;
+  p->max_images = max_images;
+  p->unit_w = kDefaultUnitW;
+  p->unit_h = kDefaultUnitH;
+  p->ctas_per_sm = 2;
+  if (cudaSetDevice(device) != cudaSuccess || cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
+    delete p;
+    return FX_ERR_CUDA;
+  }
+  bool ok = cudaMalloc(&p->d_table, table_bytes(max_images)) == cudaSuccess &&
+            cudaMalloc(&p->d_counter, 8) == cudaSuccess && cudaMalloc(&p->d_status, 4) == cudaSuccess &&
+            cudaMemset(p->d_status, 0, 4) == cudaSuccess;
+  for (int i = 0; i < 2 && ok; ++i) {
+    ok = cudaMallocHost(&p->h_table[i], table_bytes(max_images)) == cudaSuccess &&
+         cudaEventCreateWithFlags(&p->h_free[i], cudaEventDisableTiming) == cudaSuccess;
+    if (ok) std::memset(p->h_table[i], 0, table_bytes(max_images));
+  }
+  ok = ok && cudaStreamCreateWithFlags(&p->s_h2d, cudaStreamNonBlocking) == cudaSuccess &&
+       cudaStreamCreateWithFlags(&p->s_comp, cudaStreamNonBlocking) == cudaSuccess &&
+       cudaStreamCreateWithFlags(&p->s_d2h, cudaStreamNonBlocking) == cudaSuccess;
+  for (int i = 0; i < 2 && ok; ++i)
+    ok = cudaEventCreateWithFlags(&p->ev_in[i], cudaEventDisableTiming) == cudaSuccess &&
+         cudaEventCreateWithFlags(&p->ev_comp[i], cudaEventDisableTiming) == cudaSuccess &&
+         cudaEventCreateWithFlags(&p->ev_out[i], cudaEventDisableTiming) == cudaSuccess;
+  if (!ok || rebuild(p) != FX_OK) {
+    fx_plan_destroy(p);
+    return ok ? FX_ERR_CUDA : FX_ERR_NOMEM;
+  }
+  *out = p;
+  return FX_OK;
+}
+
+fx_status fx_plan_destroy(fx_plan *p) {
+  if (!p) return FX_ERR_INVALID_ARG;
+  cudaSetDevice(p->device);
+  for (int i = 0; i < 2; ++i)
+    if (p->h_free[i]) cudaEventSynchronize(p->h_free[i]);
+  if (p->s_h2d) cudaStreamSynchronize(p->s_h2d);
+  if (p->s_comp) cudaStreamSynchronize(p->s_comp);
+  if (p->s_d2h) cudaStreamSynchronize(p->s_d2h);
+  destroy_graphs(p);
+  free_host_path(p);
+  for (int i = 0; i < 2; ++i) {
+    if (p->h_table[i]) cudaFreeHost(p->h_table[i]);
+    if (p->h_free[i]) cudaEventDestroy(p->h_free[i]);
+    if (p->ev_in[i]) cudaEventDestroy(p->ev_in[i]);
+    if (p->ev_comp[i]) cudaEventDestroy(p->ev_comp[i]);
+    if (p->ev_out[i]) cudaEventDestroy(p->ev_out[i]);
+  }
+  if (p->d_table) cudaFree(p->d_table);
+  if (p->d_counter) cudaFree(p->d_counter);
+  if (p->d_status) cudaFree(p->d_status);
+  if (p->s_h2d) cudaStreamDestroy(p->s_h2d);
+  if (p->s_comp) cudaStreamDestroy(p->s_comp);
+  if (p->s_d2h) cudaStreamDestroy(p->s_d2h);
+  delete p;
+  return FX_OK;
+}
+
+fx_status fx_extract_batch(fx_plan *p, const fx_image_desc *descs, int32_t n, void *stream) {
+  if (!p || !descs || n < 1 || n > p->max_images) return FX_ERR_INVALID_ARG;
+  if (cudaSetDevice(p->device) != cudaSuccess) return FX_ERR_CUDA;
+  const int i = p->h_next;
+  // the previous replay that read host table i must have copied it out
+  if (cudaEventSynchronize(p->h_free[i]) != cudaSuccess) return FX_ERR_CUDA;
+  fx_status st = fill_table(p, p->h_table[i], descs, n);
+  if (st != FX_OK) return st;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (cudaGraphLaunch(p->graph[i], s) != cudaSuccess) return FX_ERR_CUDA;
+  if (cudaEventRecord(p->h_free[i], s) != cudaSuccess) return FX_ERR_CUDA;
+  p->h_next = i ^ 1;
+  return FX_OK;
+}
+
+fx_status fx_plan_set_tile(fx_plan *p, int32_t tile_w, int32_t tile_h, int32_t ctas_per_sm) {
+  if (!p || ctas_per_sm < 1 || ctas_per_sm > 8) return FX_ERR_INVALID_ARG;
+  if (!fast_unit_shape_ok(tile_w, tile_h)) return FX_ERR_INVALID_ARG;
+  if (cudaSetDevice(p->device) != cudaSuccess) return FX_ERR_CUDA;
+  for (int i = 0; i < 2; ++i)
+    if (cudaEventSynchronize(p->h_free[i]) != cudaSuccess) return FX_ERR_CUDA;
+  p->unit_w = tile_w;
+  p->unit_h = tile_h;
+  p->ctas_per_sm = ctas_per_sm;
+  return rebuild(p);
+}
+
+fx_status fx_plan_autotune(fx_plan *p, const fx_image_desc *descs, int32_t n, void *stream,
+                           int32_t *tile_w, int32_t *tile_h, int32_t *ctas_per_sm) {
+  if (!p || !descs || n < 1 || n > p->max_images) return FX_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return FX_ERR_CUDA;
+  float best = 1e30f;
+  int bw = p->unit_w, bh = p->unit_h, bc = p->ctas_per_sm;
+  fx_status st = FX_OK;
+  for (int c = 0; c < kNumUnitShapes && st == FX_OK; ++c) {
+    const int uw = kUnitShapes[c][0], uh = kUnitShapes[c][1];
+    for (int cps = 1; cps <= kMaxCtasPerSm && st == FX_OK; ++cps) {
+      if (!p->fast && (uw != kDefaultUnitW || uh != kDefaultUnitH)) continue;
+      if ((st = fx_plan_set_tile(p, uw, uh, cps)) != FX_OK) break;
+      int occ = 0;
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+          &occ, p->fast ? batch_kernel<true> : batch_kernel<false>, 256, p->smem);
+      if (occ < cps) continue;
+      float t_best = 1e30f;
+      for (int rep = 0; rep < 3 && st == FX_OK; ++rep) {
+        cudaEventRecord(e0, s);
+        st = fx_extract_batch(p, descs, n, s);
+        cudaEventRecord(e1, s);
+        if (cudaEventSynchronize(e1) != cudaSuccess) st = FX_ERR_CUDA;
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (rep > 0) t_best = std::min(t_best, ms);
+      }
+      if (t_best < best) {
+        best = t_best;
+        bw = uw;
+        bh = uh;
+        bc = cps;
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != FX_OK) return st;
+  st = fx_plan_set_tile(p, bw, bh, bc);
+  if (tile_w) *tile_w = bw;
+  if (tile_h) *tile_h = bh;
+  if (ctas_per_sm) *ctas_per_sm = bc;
+  return st;
+}
+
+fx_status fx_get_device_status(fx_plan *p, void *stream) {
+  if (!p) return FX_ERR_INVALID_ARG;
+  if (cudaSetDevice(p->device) != cudaSuccess) return FX_ERR_CUDA;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int h = 0;
+  if (cudaMemcpyAsync(&h, p->d_status, 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaMemsetAsync(p->d_status, 0, 4, s) != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess)
+    return FX_ERR_CUDA;
+  return h == 0 ? FX_OK : FX_ERR_INVALID_ARG;
+}
+
+// Host buffers in, host mask out.  The image goes to the device in row bands;
+// band k+1's upload overlaps band k's kernel and band k-1's download.  Each band
+// carries the input halo rows its outputs need, so results equal fx_extract's.
+fx_status fx_extract_host(fx_plan *p, const void *img_host, int64_t width, int64_t height,
+                          int64_t pitch_bytes, fx_dtype dtype, uint8_t *out_host, int64_t out_pitch) {
+  if (!p || !img_host || !out_host) return FX_ERR_INVALID_ARG;
+  if (dtype != FX_U8 && dtype != FX_U16) return FX_ERR_INVALID_ARG;
+  const int64_t elem = dtype == FX_U8 ? 1 : 2;
+  if (out_pitch == 0) out_pitch = width;
+  if (width < 1 || height < 1 || width > (1LL << 30) || height > (1LL << 30) ||
+      pitch_bytes < width * elem || pitch_bytes % elem || out_pitch < width)
+    return FX_ERR_INVALID_ARG;
+  if (dtype == FX_U16 && p->st16 != FX_OK) return p->st16;
+  const KParams &kp = dtype == FX_U8 ? p->kp8 : p->kp16;
+  if (cudaSetDevice(p->device) != cudaSuccess) return FX_ERR_CUDA;
+  const int64_t r = kp.r_in;
+  const int64_t dpitch = (width * elem + 255) / 256 * 256;
+  // bands of ~64 MiB of input, at least 64 rows
+  int64_t band = std::max<int64_t>(64, (64LL << 20) / dpitch);
+  band = std::min(band, height);
+  const int64_t in_rows = std::min(height, band + 2 * r);
+  const size_t need_in = static_cast<size_t>(in_rows * dpitch);
+  const size_t need_out = static_cast<size_t>(band * width);
+  if (need_in > p->in_cap || need_out > p->out_cap) {
+    cudaStreamSynchronize(p->s_h2d);
+    cudaStreamSynchronize(p->s_comp);
+    cudaStreamSynchronize(p->s_d2h);
+    free_host_path(p);
+    for (int i = 0; i < 2; ++i)
+      if (cudaMalloc(&p->d_in[i], need_in) != cudaSuccess || cudaMalloc(&p->d_out[i], need_out) != cudaSuccess) {
+        free_host_path(p);
+        return FX_ERR_NOMEM;
+      }
+    p->in_cap = need_in;
+    p->out_cap = need_out;
+  }
+  const unsigned char *src = static_cast<const unsigned char *>(img_host);
+  cudaError_t e = cudaSuccess;
+  int k = 0;
+  for (int64_t y0 = 0; y0 < height && e == cudaSuccess; y0 += band, ++k) {
+    const int slot = k & 1;
+    const int64_t y1 = std::min(height, y0 + band);
+    const int64_t a = std::max<int64_t>(0, y0 - r), b = std::min(height, y1 + r);
+    // slot reuse: the kernel two bands ago must be done reading d_in[slot], and
+    // the download two bands ago done reading d_out[slot]
+    e = cudaStreamWaitEvent(p->s_h2d, p->ev_comp[slot], 0);
+    if (e == cudaSuccess)
+      e = cudaMemcpy2DAsync(p->d_in[slot], dpitch, src + a * pitch_bytes, pitch_bytes, width * elem, b - a,
+                            cudaMemcpyHostToDevice, p->s_h2d);
+    if (e == cudaSuccess) e = cudaEventRecord(p->ev_in[slot], p->s_h2d);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(p->s_comp, p->ev_in[slot], 0);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(p->s_comp, p->ev_out[slot], 0);
+    if (e == cudaSuccess) {
+      ImageView v{p->d_in[slot], width, height, dpitch, a, static_cast<int32_t>(elem), p->d_out[slot], width, y0, y1};
+      e = launch_extract(v, kp, p->s_comp);
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(p->ev_comp[slot], p->s_comp);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(p->s_d2h, p->ev_comp[slot], 0);
+    if (e == cudaSuccess)
+      e = cudaMemcpy2DAsync(out_host + y0 * out_pitch, out_pitch, p->d_out[slot], width, width, y1 - y0,
+                            cudaMemcpyDeviceToHost, p->s_d2h);
+    if (e == cudaSuccess) e = cudaEventRecord(p->ev_out[slot], p->s_d2h);
+  }
+  cudaError_t e2 = cudaStreamSynchronize(p->s_d2h);
+  cudaStreamSynchronize(p->s_comp);
+  cudaStreamSynchronize(p->s_h2d);
+  return (e == cudaSuccess && e2 == cudaSuccess) ? FX_OK : FX_ERR_CUDA;
+}
+
+}  // extern "C"

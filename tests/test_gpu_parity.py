@@ -1,0 +1,246 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Integer/byte work, so the bar is bit-exactness: every compared mask byte must
+be equal.  Small and ragged cases are compared in full; the full-size scenes
+(8192^2 uint16 and one 16384^2 band, in the same launch configuration the
+benchmark times) are compared on sampled row bands that include both image
+borders, which the oracle computes on their own (its row-window mode).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from gen import scenes
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def dev_pitched(a, pitch_bytes):
+    h, w = a.shape
+    buf = torch.zeros((h, pitch_bytes // a.itemsize), dtype=torch.uint8 if a.itemsize == 1 else torch.uint16,
+                      device="cuda")
+    buf[:, :w] = dev(a)
+    return buf[:, :w]
+
+
+def pair(scale=1.0, dtype_code=None, **kw):
+    """Same parameters for the oracle (dict) and the library (fx.Params)."""
+    from paper_1304_3992_gb300 import fx
+    d = oracle.default_params(scale)
+    d.update(kw)
+    return d, fx.params_from_dict(d, dtype_code or fx.FX_U16)
+
+
+def run(cuda_lib, img, p, **kw):
+    out = cuda_lib.extract(dev(img) if not torch.is_tensor(img) else img, p, **kw)
+    torch.cuda.synchronize()
+    return out.cpu().numpy()
+
+
+def assert_same(got, ref, what=""):
+    if not np.array_equal(got, ref):
+        bad = np.argwhere(got != ref)
+        raise AssertionError(f"{what}: {len(bad)} of {ref.size} pixels differ, first at {bad[:5].tolist()}")
+
+
+def test_pan512_u8_bitexact(cuda_lib):
+    img = scenes.pan_512_u8()
+    d, p = pair(1.0)
+    ref = oracle.extract(img, d)
+    got = run(cuda_lib, img, p)
+    assert ref.sum() > 1000
+    assert_same(got, ref, "512^2 uint8")
+
+
+SHAPES = [(1, 1), (1, 37), (41, 1), (2, 2), (5, 3), (7, 33), (33, 31), (65, 97), (100, 129),
+          (31, 1000), (3, 517), (259, 6), (130, 161)]
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+@pytest.mark.parametrize("bits", [8, 12, 16])
+def test_ragged_sizes(cuda_lib, shape, bits):
+    h, w = shape
+    rng = np.random.default_rng(h * 1000 + w + bits)
+    big = scenes.scene(max(w, 16) + 20, max(h, 16) + 20, seed=int(rng.integers(1 << 30)),
+                       n_rects=max(2, w * h // 600), noise_sigma=4.0 * (1 << max(0, min(bits, 12) - 8)),
+                       impulse_frac=0.01, bits=min(bits, 12))
+    img = big[7:7 + h, 9:9 + w].copy()
+    if bits == 16:
+        img = (img.astype(np.uint32) * 16 + rng.integers(0, 16, img.shape)).astype(np.uint16)
+    scale = float(1 << max(0, bits - 8))
+    for hmf in ((5,), (), (3,)):
+        d, p = pair(scale, hmf=hmf)
+        assert_same(run(cuda_lib, img, p), oracle.extract(img, d), f"{shape} bits={bits} hmf={hmf}")
+
+
+@pytest.mark.parametrize("w", [1, 2, 31, 32, 33, 63, 64, 65, 95, 127, 129, 191, 257])
+def test_widths_mod_tile(cuda_lib, w):
+    img = scenes.scene(w + 10, 90, seed=w, n_rects=10, noise_sigma=24, impulse_frac=0.005, bits=12)[:, 5:5 + w].copy()
+    d, p = pair(16.0)
+    assert_same(run(cuda_lib, img, p), oracle.extract(img, d), f"width {w}")
+
+
+@pytest.mark.parametrize("pitch_extra", [0, 2, 256, 1000])
+def test_pitched_rows(cuda_lib, pitch_extra):
+    img = scenes.scene(301, 77, seed=3, n_rects=8, noise_sigma=24, impulse_frac=0.005, bits=12)
+    pitch = 301 * 2 + pitch_extra
+    d, p = pair(16.0)
+    got = run(cuda_lib, dev_pitched(img, pitch), p)
+    assert_same(got, oracle.extract(img, d), f"pitch {pitch}")
+
+
+def test_pitched_output(cuda_lib):
+    img = scenes.scene(150, 60, seed=4, n_rects=8, noise_sigma=4, impulse_frac=0.01, bits=8)
+    d, p = pair(1.0)
+    buf = torch.full((60, 256), 7, dtype=torch.uint8, device="cuda")
+    out = buf[:, :150]
+    cuda_lib.extract(dev(img), p, out=out)
+    torch.cuda.synchronize()
+    assert_same(out.cpu().numpy(), oracle.extract(img, d), "pitched output")
+    assert (buf[:, 150:].cpu().numpy() == 7).all(), "wrote past the row"
+
+
+@pytest.mark.parametrize("case", range(10))
+def test_parameter_variants(cuda_lib, case):
+    rng = np.random.default_rng(100 + case)
+    bits = [8, 12][case % 2]
+    img = scenes.scene(173, 141, seed=200 + case, n_rects=20, noise_sigma=4.0 * (1 << (bits - 8)),
+                       impulse_frac=0.01, bits=bits)
+    sc = float(1 << (bits - 8))
+    kw = dict(
+        t_zc=(float(rng.integers(0, 9000)) * sc, float(rng.integers(0, 30000)) * sc),
+        t_sd5=(float(rng.integers(0, 12)) * sc + 0.5, float(rng.integers(0, 12)) * sc),
+        t_sdmax=(float(rng.integers(10, 40)) * sc, float(rng.integers(10, 40)) * sc),
+        t_sd3=(float(rng.integers(0, 12)) * sc, float(rng.integers(0, 12)) * sc + 0.25),
+        hmf=[(5,), (3,), (5, 3), (), (5, 5, 3), (3, 3)][case % 6],
+        stddev_source=int(case in (3, 7)),
+        sigma=[(0.5, 20.0), (0.7, 2.0), (1.0, 5.0)][case % 3],
+    )
+    if kw["stddev_source"]:
+        kw.update(t_sd5=(0.3, 0.3), t_sdmax=(0.45, 0.45), t_sd3=(0.4, 0.4))
+    d, p = pair(sc, **kw)
+    assert_same(run(cuda_lib, img, p), oracle.extract(img, d), f"case {case}")
+
+
+def test_negative_and_extreme_thresholds(cuda_lib):
+    img = scenes.scene(120, 90, seed=8, n_rects=10, noise_sigma=24, impulse_frac=0.005, bits=12)
+    for kw in (dict(t_zc=(-5.0, -1.0), t_sd5=(-1.0, -1.0), t_sdmax=(-1.0, -1.0), t_sd3=(-1.0, -1.0)),
+               dict(t_zc=(1e30, 1e30)), dict(t_sd5=(1e300, 1e300), t_sdmax=(float("inf"),) * 2),
+               dict(t_zc=(0.0, 0.0), t_sd5=(0.0, 0.0), t_sdmax=(0.0, 0.0), t_sd3=(0.0, 0.0))):
+        d, p = pair(16.0, **kw)
+        assert_same(run(cuda_lib, img, p), oracle.extract(img, d), str(kw))
+
+
+def test_constant_and_step_images(cuda_lib):
+    d, p = pair(16.0, t_zc=(0, 0), t_sd5=(0, 0), t_sd3=(0, 0))
+    for h, w in ((1, 1), (37, 70)):
+        assert not run(cuda_lib, np.full((h, w), 4095, np.uint16), p).any()
+    step = np.full((40, 100), 1000, np.uint16)
+    step[:, 61:] = 1200
+    got = run(cuda_lib, step, p)
+    assert np.array_equal(got.any(axis=0).nonzero()[0], [61]) and got[:, 61].all()
+
+
+def test_dihedral_equivariance_gpu(cuda_lib):
+    img = scenes.scene(211, 150, seed=12, n_rects=25, noise_sigma=24, impulse_frac=0.005, bits=12)
+    _, p = pair(16.0)
+    ref = run(cuda_lib, img, p)
+    for fwd, inv in ((lambda a: a.T, lambda a: a.T), (lambda a: a[::-1], lambda a: a[::-1]),
+                     (lambda a: np.rot90(a), lambda a: np.rot90(a, -1))):
+        assert_same(inv(run(cuda_lib, np.ascontiguousarray(fwd(img)), p)), ref, "D4")
+
+
+def _sample_bands(H, k, rows, seed):
+    rng = np.random.default_rng(seed)
+    starts = [0, H - rows] + sorted(int(s) for s in rng.integers(rows, H - 2 * rows, k))
+    return [(s, s + rows) for s in starts]
+
+
+def test_ms8192_u16_sampled_rows(cuda_lib):
+    img = scenes.ms_8192_u16_11bit()
+    d, p = pair(8.0)
+    from paper_1304_3992_gb300 import fx
+    p = fx.params_from_dict(d)
+    got = run(cuda_lib, img, p)
+    assert set(np.unique(got)) <= {0, 1}
+    for y0, y1 in _sample_bands(img.shape[0], 6, 12, 1):
+        assert_same(got[y0:y1], oracle.extract(img, d, rows=(y0, y1)), f"rows {y0}:{y1}")
+    # left and right image borders over a tall band
+    assert_same(got[3000:3100, :], oracle.extract(img, d, rows=(3000, 3100)), "rows 3000:3100")
+
+
+def test_band16384_u16_sampled_rows(cuda_lib):
+    band = next(scenes.ms_bands_u16_12bit(bands=[1]))
+    d, p = pair(16.0)
+    got = run(cuda_lib, band, p)
+    for y0, y1 in _sample_bands(band.shape[0], 4, 8, 2):
+        assert_same(got[y0:y1], oracle.extract(band, d, rows=(y0, y1)), f"rows {y0}:{y1}")
+
+
+def test_batch_matches_single_and_oracle(cuda_lib):
+    batch = scenes.uneven_batch(n=10, lo=40, hi=700, seed=7, master_side=900)
+    d, p = pair(16.0)
+    d8 = oracle.default_params(16.0)
+    pairs, singles = [], []
+    for view, _ in batch:
+        img = dev(view) if view.flags.c_contiguous else dev_pitched(view, view.strides[0])
+        out = torch.full(view.shape, 9, dtype=torch.uint8, device="cuda")
+        pairs.append((img, out))
+        singles.append(run(cuda_lib, img, p))
+    with cuda_lib.Plan(p, max_images=16) as plan:
+        for rep in range(2):
+            plan.extract_batch(pairs)
+            torch.cuda.synchronize()
+            for i, ((img, out), single) in enumerate(zip(pairs, singles)):
+                assert_same(out.cpu().numpy(), single, f"batch image {i} rep {rep}")
+        assert plan.device_status() == 0
+    for i in (0, 1, 5):
+        assert_same(singles[i], oracle.extract(np.ascontiguousarray(batch[i][0]), d8), f"oracle image {i}")
+
+
+def test_batch_autotune_keeps_results(cuda_lib):
+    batch = scenes.uneven_batch(n=6, lo=100, hi=900, seed=8, master_side=1000)
+    _, p = pair(16.0)
+    pairs = [(dev_pitched(v, v.strides[0]), torch.zeros(v.shape, dtype=torch.uint8, device="cuda")) for v, _ in batch]
+    singles = [run(cuda_lib, img, p) for img, _ in pairs]
+    with cuda_lib.Plan(p, max_images=8) as plan:
+        cfg = plan.autotune(pairs)
+        assert cfg[2] >= 1
+        for o in pairs:
+            o[1].zero_()
+        plan.extract_batch(pairs)
+        torch.cuda.synchronize()
+        for (img, out), single in zip(pairs, singles):
+            assert_same(out.cpu().numpy(), single, f"after autotune {cfg}")
+
+
+def test_extract_host_matches_device(cuda_lib):
+    img = scenes.scene(1500, 1300, seed=31, n_rects=200, noise_sigma=24, impulse_frac=0.005, bits=12)
+    _, p = pair(16.0)
+    ref = run(cuda_lib, img, p)
+    with cuda_lib.Plan(p, max_images=1) as plan:
+        got = plan.extract_host(img)
+        assert_same(got, ref, "host path")
+        img8 = scenes.scene(999, 700, seed=32, n_rects=90, noise_sigma=4, impulse_frac=0.01, bits=8)
+        assert_same(plan.extract_host(img8), run(cuda_lib, img8, p), "host path u8")
+
+
+def test_device_pointer_checks(cuda_lib):
+    import ctypes
+    from paper_1304_3992_gb300 import fx
+    lib = fx.load()
+    p = fx.make_params(fx.FX_U16)
+    host = np.zeros((8, 8), np.uint16)
+    out = torch.zeros((8, 8), dtype=torch.uint8, device="cuda")
+    assert lib.fx_extract(host.ctypes.data, 8, 8, 16, fx.FX_U16, ctypes.byref(p), out.data_ptr(), None) == 1
+    q = fx.make_params(fx.FX_U16, mask_q=1 << 20)
+    img = torch.zeros((8, 8), dtype=torch.uint16, device="cuda")
+    assert lib.fx_extract(img.data_ptr(), 8, 8, 16, fx.FX_U16, ctypes.byref(q), out.data_ptr(), None) == 3
+    nanp = fx.make_params(fx.FX_U16, t_zc=(float("nan"), 0.0))
+    assert lib.fx_extract(img.data_ptr(), 8, 8, 16, fx.FX_U16, ctypes.byref(nanp), out.data_ptr(), None) == 1
