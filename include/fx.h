@@ -189,6 +189,28 @@ fx_status fx_extract_host(fx_plan *plan, const void *img_host, int64_t width, in
                           int64_t pitch_bytes, fx_dtype dtype, uint8_t *out_mask_host,
                           int64_t out_pitch);
 
+/*
+ * Batched extraction for callers that cannot allocate device memory.  The
+ * paper has no counterpart; this entry point exists for deployment.  It does
+ * what fx_extract_batch does (same masks, byte for byte) without a plan: its
+ * only scratch (descriptor table and tile-queue counter, about 8 KiB) is a
+ * fixed array inside the library that every GPU loading libfx.so reserves
+ * until process exit.  The call itself allocates nothing on host or device.
+ *   params  NULL = fx_params_default(FX_U16, 0)
+ *   descs   HOST array of n descriptors, validated like fx_extract's arguments
+ *   n       1 .. FX_NOALLOC_MAX_IMAGES; a larger n returns FX_ERR_BUDGET and
+ *           launches nothing
+ * The first call on a device looks up the scratch array's device address
+ * (once per device, with that device current); make that first call before
+ * any stream capture.  Every call on a device shares the one array and leaves
+ * its contents behind (each call resets the queue counter itself), so calls
+ * whose work overlaps on the GPU race: serialise them (one stream, or events).
+ * Errors: FX_ERR_INVALID_ARG, FX_ERR_RANGE, FX_ERR_BUDGET, FX_ERR_CUDA.
+ */
+#define FX_NOALLOC_MAX_IMAGES 128
+fx_status fx_extract_batch_noalloc(const fx_params *params, const fx_image_desc *descs, int32_t n,
+                                   void *stream);
+
 /* Human-readable name of a status code (static storage). */
 const char *fx_status_string(fx_status s);
 

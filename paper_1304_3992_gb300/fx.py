@@ -75,6 +75,8 @@ _SIGNATURES = {
     "fx_get_device_status": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "fx_extract_host": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
                                        ctypes.c_int64, ctypes.c_int, ctypes.c_void_p, ctypes.c_int64]),
+    "fx_extract_batch_noalloc": (ctypes.c_int, [ctypes.POINTER(Params), ctypes.POINTER(ImageDesc),
+                                                ctypes.c_int32, ctypes.c_void_p]),
     "fx_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "fx_version": (ctypes.c_char_p, []),
 }
