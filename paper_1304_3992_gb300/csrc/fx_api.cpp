@@ -75,6 +75,27 @@ fx_status make_kparams(const fx_params *p, int32_t maxval, KParams *kp) {
   kp->splus = splus;
   // |L| <= maxval * splus for every partial sum; the contrast needs twice that.
   if (2 * static_cast<int64_t>(maxval) * splus >= INT32_MAX) return FX_ERR_RANGE;
+  // FP32 path: partial sums of L below 2^24 and D below 2^32 (values <= 4095).
+  int64_t fb = splus > 0 ? ((1LL << 24) - 1) / splus : 4095;
+  if (fb > 4095) fb = 4095;
+  kp->fbound = static_cast<int32_t>(fb);
+  for (int f = 0; f < 2; ++f) {
+    // max - min < 2^25 on the FP32 path; tzc + 1 must be exact or out of reach
+    const int64_t t1 = static_cast<int64_t>(kp->tzc[f]) + 1;
+    if (t1 <= (1LL << 24)) kp->tzc1f[f] = static_cast<float>(t1);
+    else if (t1 >= (1LL << 25)) kp->tzc1f[f] = 33554432.0f;
+    else kp->fbound = -1;
+    auto tt = [](int64_t t) -> uint32_t {  // D > t  <=>  D >= t + 1 (D < 2^32)
+      if (t < 0) return 0u;
+      if (t >= 0xFFFFFFFFLL) return 0xFFFFFFFFu;
+      return static_cast<uint32_t>(t + 1);
+    };
+    kp->tt5[f] = tt(kp->tsd5[f]);
+    kp->ttmax[f] = tt(kp->tsdmax[f]);
+    kp->tt3[f] = tt(kp->tsd3[f]);
+    kp->fixzero[f] = kp->ring[f][5] > 0 ? 0 : 1;
+  }
+  kp->sd_same = kp->tsd5[0] == kp->tsd5[1] && kp->tsdmax[0] == kp->tsdmax[1] && kp->tsd3[0] == kp->tsd3[1];
   return FX_OK;
 }
 
@@ -182,7 +203,7 @@ fx_status fx_extract(const void *img, int64_t width, int64_t height, int64_t pit
   KParams kp;
   st = make_kparams(params, dtype == FX_U8 ? 255 : 65535, &kp);
   if (st != FX_OK) return st;
-  ImageView v{img, width, height, pitch_bytes, 0, dtype == FX_U8 ? 1 : 2, out_mask, out_pitch, 0, height};
+  ImageView v{img, width, height, pitch_bytes, 0, dtype == FX_U8 ? 1 : 2, out_mask, out_pitch, 0, height, height};
   return launch_extract(v, kp, static_cast<cudaStream_t>(stream)) == cudaSuccess ? FX_OK : FX_ERR_CUDA;
 }
 

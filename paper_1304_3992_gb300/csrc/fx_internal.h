@@ -27,6 +27,16 @@ struct KParams {
   int32_t r_in;    // input radius of one output pixel
   // Largest sum of positive taps over both masks; bounds |L| <= maxval * splus.
   int64_t splus;
+  // --- streaming fast path (fx_stream.cuh) ---
+  // Largest input value for which the FP32 evaluation is exact (every LoG
+  // partial sum below 2^24, D below 2^32, t_zc + 1 representable); -1 = never.
+  int32_t fbound;
+  // FP32 contrast test: (max - min) - tzc1f < 0  <=>  max - min <= t_zc.
+  float tzc1f[2];
+  // 32-bit standard-deviation tests for the FP32 path: s > T  <=>  D >= tt.
+  uint32_t tt5[2], ttmax[2], tt3[2];
+  int32_t sd_same;   // both branches use the same standard-deviation thresholds
+  int32_t fixzero[2];  // outer-ring weight not positive: canonicalise -0 after the sum
 };
 
 // Derive KParams from fx_params for images whose values are <= maxval.
@@ -42,11 +52,12 @@ fx_status check_image(const void *img, int64_t width, int64_t height, int64_t pi
 struct ImageView {
   const void *img;
   int64_t width, height, pitch;  // pitch in bytes
-  int64_t row0;
+  int64_t row0;                  // image row held at img
   int32_t elem;                  // 1 or 2
   uint8_t *out;
   int64_t out_pitch;
   int64_t y_begin, y_end;
+  int64_t row_lim;               // rows [row0, row_lim) are present in the buffer
 };
 
 cudaError_t launch_tile_general(const ImageView &v, const KParams &kp, cudaStream_t s);

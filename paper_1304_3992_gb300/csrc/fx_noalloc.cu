@@ -94,7 +94,7 @@ __global__ void __launch_bounds__(gen::NT) noalloc_batch_kernel(unsigned char *s
     }
     const NoAllocImage &b = ims[lo];
     const long long local = u - b.unit_begin;
-    ImageView v{b.img, b.width, b.height, b.pitch, 0, b.elem, b.out, b.out_pitch, 0, b.height};
+    ImageView v{b.img, b.width, b.height, b.pitch, 0, b.elem, b.out, b.out_pitch, 0, b.height, b.height};
     const int64_t ux = local % b.units_x, uy = local / b.units_x;
     if (b.elem == 1) gen::general_tile<uint8_t>(v, kp8, ux * gen::TW, uy * gen::TH, smem);
     else gen::general_tile<uint16_t>(v, kp16, ux * gen::TW, uy * gen::TH, smem);

@@ -37,47 +37,100 @@ size_t table_bytes(int max_images) { return sizeof(BatchHeader) + sizeof(BatchIm
 // Status bits written by the batch kernel.
 constexpr int kStatusBadDescriptor = 1;
 
-// Persistent kernel: CTAs pop work units (one output tile / strip segment of
-// one image) from a global counter until the queue is empty.  Units of
-// different images and dtypes interleave freely.
-template <bool kFast>
-__global__ void __launch_bounds__(256) batch_kernel(const unsigned char *table,
-                                                    unsigned long long *counter, int *status,
-                                                    KParams kp8, KParams kp16) {
+// Persistent kernels: CTAs (general tile) or warps (streaming strip) pop work
+// units -- one output tile / strip segment of one image -- from a global
+// counter until the queue is empty.  Units of different images and dtypes
+// interleave freely; the image is found by binary search over unit offsets.
+__device__ __forceinline__ int find_image(const BatchImage *ims, int n, long long u) {
+  int lo = 0, hi = n - 1;  // last image whose first unit is <= u
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (ims[mid].unit_begin <= u) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ ImageView view_of(const BatchImage &b) {
+  return ImageView{b.img, b.width, b.height, b.pitch, 0, b.elem, b.out, b.out_pitch, 0, b.height, b.height};
+}
+
+__global__ void __launch_bounds__(256) batch_kernel_general(const unsigned char *table,
+                                                            unsigned long long *counter, int *status,
+                                                            const __grid_constant__ KParams kp8,
+                                                            const __grid_constant__ KParams kp16) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ long long s_unit;
   const BatchHeader *hdr = reinterpret_cast<const BatchHeader *>(table);
   const BatchImage *ims = reinterpret_cast<const BatchImage *>(table + sizeof(BatchHeader));
   const long long total = hdr->total_units;
-  const int n = hdr->n;
   for (;;) {
     if (threadIdx.x == 0) s_unit = static_cast<long long>(atomicAdd(counter, 1ULL));
     __syncthreads();
     const long long u = s_unit;
     __syncthreads();
     if (u >= total) break;
-    int lo = 0, hi = n - 1;  // last image whose first unit is <= u
-    while (lo < hi) {
-      int mid = (lo + hi + 1) >> 1;
-      if (ims[mid].unit_begin <= u) lo = mid;
-      else hi = mid - 1;
-    }
-    const BatchImage &b = ims[lo];
-    const long long local = u - b.unit_begin;
+    const BatchImage &b = ims[find_image(ims, hdr->n, u)];
     if (b.units_x <= 0 || (b.elem != 1 && b.elem != 2)) {
       if (threadIdx.x == 0) atomicOr(status, kStatusBadDescriptor);
       continue;
     }
-    ImageView v{b.img, b.width, b.height, b.pitch, 0, b.elem, b.out, b.out_pitch, 0, b.height};
+    const ImageView v = view_of(b);
+    const long long local = u - b.unit_begin;
     const int64_t ux = local % b.units_x, uy = local / b.units_x;
-    if constexpr (kFast) {
-      if (b.elem == 1) fast_unit<uint8_t>(v, kp8, ux, uy, hdr->unit_w, hdr->unit_h, smem);
-      else fast_unit<uint16_t>(v, kp16, ux, uy, hdr->unit_w, hdr->unit_h, smem);
-    } else {
-      if (b.elem == 1) gen::general_tile<uint8_t>(v, kp8, ux * gen::TW, uy * gen::TH, smem);
-      else gen::general_tile<uint16_t>(v, kp16, ux * gen::TW, uy * gen::TH, smem);
-    }
+    if (b.elem == 1) gen::general_tile<uint8_t>(v, kp8, ux * gen::TW, uy * gen::TH, smem);
+    else gen::general_tile<uint16_t>(v, kp16, ux * gen::TW, uy * gen::TH, smem);
     __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(32 * kWarpsPerCta) batch_kernel_fast(const unsigned char *table,
+                                                                      unsigned long long *counter, int *status,
+                                                                      const __grid_constant__ KParams kp8,
+                                                                      const __grid_constant__ KParams kp16) {
+  const BatchHeader *hdr = reinterpret_cast<const BatchHeader *>(table);
+  const BatchImage *ims = reinterpret_cast<const BatchImage *>(table + sizeof(BatchHeader));
+  const long long total = hdr->total_units;
+  const int lane = threadIdx.x & 31;
+  for (;;) {
+    unsigned long long got = 0;
+    if (lane == 0) got = atomicAdd(counter, 1ULL);
+    const long long u = static_cast<long long>(__shfl_sync(0xffffffffu, got, 0));
+    if (u >= total) break;
+    const BatchImage &b = ims[find_image(ims, hdr->n, u)];
+    if (b.units_x <= 0 || (b.elem != 1 && b.elem != 2)) {
+      if (lane == 0) atomicOr(status, kStatusBadDescriptor);
+      continue;
+    }
+    const ImageView v = view_of(b);
+    const long long local = u - b.unit_begin;
+    const int64_t ux = local % b.units_x, uy = local / b.units_x;
+    if (b.elem == 1) fast_unit<uint8_t>(v, kp8, ux, uy, hdr->unit_w, hdr->unit_h, nullptr);
+    else fast_unit<uint16_t>(v, kp16, ux, uy, hdr->unit_w, hdr->unit_h, nullptr);
+  }
+}
+
+// Second pass of the streaming path: every warp walks the units with a static
+// stride and recomputes, on the integer path, the strips the first pass marked.
+__global__ void __launch_bounds__(32 * kWarpsPerCta) batch_kernel_redo(const unsigned char *table,
+                                                                      unsigned long long *, int *,
+                                                                      const __grid_constant__ KParams kp8,
+                                                                      const __grid_constant__ KParams kp16) {
+  const BatchHeader *hdr = reinterpret_cast<const BatchHeader *>(table);
+  const BatchImage *ims = reinterpret_cast<const BatchImage *>(table + sizeof(BatchHeader));
+  const long long total = hdr->total_units;
+  const long long warps = static_cast<long long>(gridDim.x) * kWarpsPerCta;
+  for (long long u = static_cast<long long>(blockIdx.x) * kWarpsPerCta + (threadIdx.x >> 5); u < total; u += warps) {
+    const BatchImage &b = ims[find_image(ims, hdr->n, u)];
+    if (b.units_x <= 0 || (b.elem != 1 && b.elem != 2)) continue;
+    const ImageView v = view_of(b);
+    const long long local = u - b.unit_begin;
+    const int64_t ux = local % b.units_x, uy = local / b.units_x;
+    if (b.elem == 1) {
+      if (kp8.fbound < 0 || kp8.fbound < 255) fast_unit_redo<uint8_t>(v, kp8, ux, uy, hdr->unit_w, hdr->unit_h, nullptr);
+    } else {
+      fast_unit_redo<uint16_t>(v, kp16, ux, uy, hdr->unit_w, hdr->unit_h, nullptr);
+    }
   }
 }
 
@@ -129,8 +182,8 @@ size_t unit_smem(const fx_plan *p) {
 // persistent kernel.  The table copy has a fixed size so the graph never changes.
 fx_status build_graph(fx_plan *p, int i) {
   p->smem = unit_smem(p);
-  const void *fn = p->fast ? reinterpret_cast<const void *>(&batch_kernel<true>)
-                           : reinterpret_cast<const void *>(&batch_kernel<false>);
+  const void *fn = p->fast ? reinterpret_cast<const void *>(&batch_kernel_fast)
+                           : reinterpret_cast<const void *>(&batch_kernel_general);
   if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) != cudaSuccess)
     return FX_ERR_CUDA;
   cudaGraph_t g;
@@ -159,12 +212,19 @@ fx_status build_graph(fx_plan *p, int i) {
   std::memset(&kn, 0, sizeof kn);
   kn.func = const_cast<void *>(fn);
   kn.gridDim = dim3(static_cast<unsigned>(p->num_sms * p->ctas_per_sm));
-  kn.blockDim = dim3(256);
+  kn.blockDim = dim3(p->fast ? 32 * kWarpsPerCta : 256);
   kn.sharedMemBytes = static_cast<unsigned>(p->smem);
   kn.kernelParams = args;
   cudaError_t e = cudaGraphAddMemcpyNode(&n_copy, g, nullptr, 0, &cp);
   if (e == cudaSuccess) e = cudaGraphAddMemsetNode(&n_zero, g, &n_copy, 1, &ms);
   if (e == cudaSuccess) e = cudaGraphAddKernelNode(&n_kern, g, &n_zero, 1, &kn);
+  if (e == cudaSuccess && p->fast) {  // integer redo pass of the streaming path
+    cudaKernelNodeParams kr = kn;
+    kr.func = reinterpret_cast<void *>(&batch_kernel_redo);
+    kr.sharedMemBytes = 0;
+    cudaGraphNode_t n_redo;
+    e = cudaGraphAddKernelNode(&n_redo, g, &n_kern, 1, &kr);
+  }
   if (e == cudaSuccess) e = cudaGraphInstantiate(&p->graph[i], g, 0);
   cudaGraphDestroy(g);
   return e == cudaSuccess ? FX_OK : FX_ERR_CUDA;
@@ -183,6 +243,7 @@ fx_status fill_table(fx_plan *p, unsigned char *h, const fx_image_desc *d, int32
   BatchHeader *hdr = reinterpret_cast<BatchHeader *>(h);
   BatchImage *ims = reinterpret_cast<BatchImage *>(h + sizeof(BatchHeader));
   const int uw = p->fast ? p->unit_w : gen::TW, uh = p->fast ? p->unit_h : gen::TH;
+  const int uwx = p->fast ? kDefaultUnitW : gen::TW;  // output columns per unit
   int64_t total = 0;
   for (int32_t i = 0; i < n; ++i) {
     const int64_t op = d[i].out_pitch ? d[i].out_pitch : d[i].width;
@@ -199,7 +260,7 @@ fx_status fill_table(fx_plan *p, unsigned char *h, const fx_image_desc *d, int32
     b.out_pitch = op;
     b.elem = d[i].dtype == FX_U8 ? 1 : 2;
     b.pad = 0;
-    b.units_x = (b.width + uw - 1) / uw;
+    b.units_x = (b.width + uwx - 1) / uwx;
     b.unit_begin = total;
     total += b.units_x * ((b.height + uh - 1) / uh);
   }
@@ -356,8 +417,8 @@ fx_status fx_plan_autotune(fx_plan *p, const fx_image_desc *descs, int32_t n, vo
       if (!p->fast && (uw != kDefaultUnitW || uh != kDefaultUnitH)) continue;
       if ((st = fx_plan_set_tile(p, uw, uh, cps)) != FX_OK) break;
       int occ = 0;
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-          &occ, p->fast ? batch_kernel<true> : batch_kernel<false>, 256, p->smem);
+      if (p->fast) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batch_kernel_fast, 32 * kWarpsPerCta, 0);
+      else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batch_kernel_general, 256, p->smem);
       if (occ < cps) continue;
       float t_best = 1e30f;
       for (int rep = 0; rep < 3 && st == FX_OK; ++rep) {
@@ -451,7 +512,7 @@ fx_status fx_extract_host(fx_plan *p, const void *img_host, int64_t width, int64
     if (e == cudaSuccess) e = cudaStreamWaitEvent(p->s_comp, p->ev_in[slot], 0);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(p->s_comp, p->ev_out[slot], 0);
     if (e == cudaSuccess) {
-      ImageView v{p->d_in[slot], width, height, dpitch, a, static_cast<int32_t>(elem), p->d_out[slot], width, y0, y1};
+      ImageView v{p->d_in[slot], width, height, dpitch, a, static_cast<int32_t>(elem), p->d_out[slot], width, y0, y1, b};
       e = launch_extract(v, kp, p->s_comp);
     }
     if (e == cudaSuccess) e = cudaEventRecord(p->ev_comp[slot], p->s_comp);

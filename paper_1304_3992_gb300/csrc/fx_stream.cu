@@ -1,12 +1,46 @@
-// fx_stream.cu -- launch of the streaming fast path (placeholder).
+// fx_stream.cu -- grid launch of the streaming fast path (fx_stream.cuh).
 #include "fx_stream.cuh"
 
 namespace fx {
+namespace {
 
-bool fast_path_supported(const KParams &) { return false; }
+template <typename T, bool kRedoPass>
+__global__ void __launch_bounds__(32 * kWarpsPerCta) stream_kernel(const __grid_constant__ ImageView v,
+                                                                  const __grid_constant__ KParams kp,
+                                                                  int64_t units_x, int64_t units, int uh) {
+  const int64_t unit = static_cast<int64_t>(blockIdx.x) * kWarpsPerCta + (threadIdx.x >> 5);
+  if (unit >= units) return;  // whole warps only
+  if constexpr (kRedoPass) fast_unit_redo<T>(v, kp, unit % units_x, unit / units_x, kDefaultUnitW, uh, nullptr);
+  else fast_unit<T>(v, kp, unit % units_x, unit / units_x, kDefaultUnitW, uh, nullptr);
+}
+
+template <typename T>
+cudaError_t launch_t(const ImageView &v, const KParams &kp, cudaStream_t s, int64_t blocks, int64_t units_x,
+                     int64_t units, int uh) {
+  if (kp.fbound >= 0)
+    stream_kernel<T, false><<<static_cast<unsigned>(blocks), 32 * kWarpsPerCta, 0, s>>>(v, kp, units_x, units, uh);
+  // the integer pass recomputes the strips the FP32 pass marked (all when fbound < 0)
+  if (kp.fbound < 0 || kp.fbound < (sizeof(T) == 1 ? 255 : 65535))
+    stream_kernel<T, true><<<static_cast<unsigned>(blocks), 32 * kWarpsPerCta, 0, s>>>(v, kp, units_x, units, uh);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+// The streaming kernel covers the default configuration: image source for the
+// standard deviation and at most one median pass.
+bool fast_path_supported(const KParams &kp) { return kp.source == 0 && kp.nhmf <= 1; }
 
 cudaError_t launch_fast(const ImageView &v, const KParams &kp, cudaStream_t s) {
-  return launch_tile_general(v, kp, s);
+  const int uh = kDefaultUnitH;
+  const int64_t units_x = (v.width + kDefaultUnitW - 1) / kDefaultUnitW;
+  const int64_t units_y = (v.y_end - v.y_begin + uh - 1) / uh;
+  const int64_t units = units_x * units_y;
+  if (units <= 0) return cudaSuccess;
+  const int64_t blocks = (units + kWarpsPerCta - 1) / kWarpsPerCta;
+  if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
+  return v.elem == 1 ? launch_t<uint8_t>(v, kp, s, blocks, units_x, units, uh)
+                     : launch_t<uint16_t>(v, kp, s, blocks, units_x, units, uh);
 }
 
 }  // namespace fx

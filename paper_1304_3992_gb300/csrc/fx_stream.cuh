@@ -1,29 +1,579 @@
-// fx_stream.cuh -- the streaming fast path (device code).  Placeholder until
-// the specialised kernel lands: routes every unit to the general tile.
+// fx_stream.cuh -- the streaming fast path (device code).
+//
+// One warp computes a strip of 112 output columns over a range of output rows,
+// walking down the image one row per step.  Lane l owns the four adjacent
+// window columns xs + 4l .. xs + 4l + 3 of a 128-column window that starts 8
+// columns left of the strip (the halo the stages need: 2 LoG + 1 crossing +
+// 2 median, rounded up to the 8-column alignment of the loads).
+//
+// Per step (one input row t; every value stays in registers):
+//   - one coalesced load of the lane's 4 pixels (plus 2 + 2 halo pixels from
+//     the neighbouring lanes by shuffle);
+//   - horizontal sums h1 = I(x-1) + I(x+1), h2 = I(x-2) + I(x+2) and the
+//     3- and 5-wide sums of squares (integer);
+//   - for the centre row c = t-2: the six ring sums R0..R8 of the radial
+//     masks (squared radii 0, 1, 2, 4, 5, 8), L_f = sum_c w_fc R_c for both
+//     masks (Eq. 1, reading R1), and the standard-deviation test of Eq. 2 from
+//     exact sums (reading R4);
+//   - for row c' = t-3 (whose four neighbours are now known): the sign of L,
+//     the sign of -L, the signs of the east and south edge sums L(p)+L(q) and
+//     the contrast test (Sec. 3.2), each packed as one bit per pixel.
+// Bits are packed into 32-bit words covering 8 rows x the lane's 4 columns
+// (bit 28 - 4r + j for row r, column j).  Every 8 rows the zero-crossing rule
+// (reading R3), the extraction, the OR of the two maps (Sec. 4.1) and the
+// hybrid median (Sec. 3.4, reading R6) run as bitwise logic on those words,
+// and the finished mask rows are stored.
+//
+// Arithmetic is exact: the FP32 path is used while every input value is at
+// most KParams::fbound (all LoG partial sums below 2^24, Eq. 2's D below
+// 2^32); a strip that meets a larger value is recomputed on the integer path
+// (int32 LoG, int64 D).  Borders follow reading R2 (every stage replicated):
+// loads clamp, and the L values and mask bits of rows / columns outside the
+// image are replaced by those of the nearest image row / column.
 #pragma once
+#include <cstdint>
+
 #include "fx_internal.h"
-#include "fx_tile.cuh"
 
 namespace fx {
 
-constexpr int kDefaultUnitW = gen::TW;
-constexpr int kDefaultUnitH = gen::TH;
-constexpr int kNumUnitShapes = 1;
-constexpr int kUnitShapes[kNumUnitShapes][2] = {{gen::TW, gen::TH}};
-constexpr int kMaxCtasPerSm = 4;
+constexpr int kDefaultUnitW = 112;
+constexpr int kDefaultUnitH = 512;
+constexpr int kNumUnitShapes = 4;
+constexpr int kUnitShapes[kNumUnitShapes][2] = {{112, 256}, {112, 512}, {112, 1024}, {112, 2048}};
+constexpr int kMaxCtasPerSm = 8;
+constexpr int kWarpsPerCta = 4;
 
-inline bool fast_unit_shape_ok(int w, int h) { return w == gen::TW && h == gen::TH; }
+inline bool fast_unit_shape_ok(int w, int h) { return w == 112 && h >= 8 && h <= 8192 && h % 8 == 0; }
+inline size_t fast_smem_bytes(int, int, int) { return 0; }
 
-inline size_t fast_smem_bytes(int r_in, int, int) {
-  KParams kp{};
-  kp.r_m = r_in - 5;
-  return gen::general_smem_bytes(kp);
+namespace st {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kLeftHalo = 8;
+constexpr int kOutCols = 112;
+constexpr uint32_t MJ0 = 0x11111111u, MJ3 = 0x88888888u, MJ01 = 0x33333333u, MJ23 = 0xCCCCCCCCu;
+
+// Neighbour words: bit of pixel p in the result = bit of its neighbour.
+// own = this lane's word, nx / pv = the next / previous lane's word of the same
+// rows, nb / pb = this lane's word of the next / previous 8 rows.
+__device__ __forceinline__ uint32_t e1(uint32_t o, uint32_t nx) { return ((o >> 1) & ~MJ3) | ((nx << 3) & MJ3); }
+__device__ __forceinline__ uint32_t w1(uint32_t o, uint32_t pv) { return ((o << 1) & ~MJ0) | ((pv >> 3) & MJ0); }
+__device__ __forceinline__ uint32_t e2(uint32_t o, uint32_t nx) { return ((o >> 2) & MJ01) | ((nx << 2) & MJ23); }
+__device__ __forceinline__ uint32_t w2(uint32_t o, uint32_t pv) { return ((o << 2) & MJ23) | ((pv >> 2) & MJ01); }
+__device__ __forceinline__ uint32_t n1(uint32_t o, uint32_t pb) { return (o >> 4) | (pb << 28); }
+__device__ __forceinline__ uint32_t s1(uint32_t o, uint32_t nb) { return (o << 4) | (nb >> 28); }
+__device__ __forceinline__ uint32_t n2(uint32_t o, uint32_t pb) { return (o >> 8) | (pb << 24); }
+__device__ __forceinline__ uint32_t s2(uint32_t o, uint32_t nb) { return (o << 8) | (nb >> 24); }
+
+__device__ __forceinline__ void fadd(uint32_t a, uint32_t b, uint32_t c, uint32_t &s, uint32_t &k) {
+  s = a ^ b ^ c;
+  k = (a & b) | (c & (a ^ b));
+}
+__device__ __forceinline__ uint32_t maj3(uint32_t a, uint32_t b, uint32_t c) { return (a & b) | (c & (a | b)); }
+// bitwise "at least 5 of 9"
+__device__ __forceinline__ uint32_t maj9(const uint32_t x[9]) {
+  uint32_t s1, c1, s2, c2, s3, c3, s4, c4;
+  fadd(x[0], x[1], x[2], s1, c1);
+  fadd(x[3], x[4], x[5], s2, c2);
+  fadd(x[6], x[7], x[8], s3, c3);
+  fadd(s1, s2, s3, s4, c4);
+  const uint32_t at2 = (c1 & c2) | (c3 & c4) | ((c1 | c2) & (c3 | c4));
+  const uint32_t at3 = (c1 & c2 & (c3 | c4)) | (c3 & c4 & (c1 | c2));
+  return at3 | (at2 & s4);
+}
+// bitwise "at least 3 of 5"
+__device__ __forceinline__ uint32_t maj5(const uint32_t x[5]) {
+  uint32_t s1, c1, s2, c2;
+  fadd(x[0], x[1], x[2], s1, c1);
+  fadd(x[3], x[4], s1, s2, c2);
+  return (c1 & c2) | ((c1 | c2) & s2);
+}
+
+// Pack the sign bit of v into an accumulator (shift-left insertion).
+__device__ __forceinline__ void put(uint32_t &acc, uint32_t v) { acc = __funnelshift_l(v, acc, 1); }
+
+template <bool kInt>
+struct Ar;
+
+// FP32 path: values <= fbound, every intermediate an exact FP32 integer.
+template <>
+struct Ar<false> {
+  using V = float;
+  using Q = uint32_t;
+  static __device__ __forceinline__ V cvt(uint32_t u) { return __uint_as_float(0x4B000000u | u) - 8388608.0f; }
+  static __device__ __forceinline__ Q sq(uint32_t u) { return u * u; }
+  static __device__ __forceinline__ V w(const KParams &kp, int f, int c) { return kp.ringf[f][c]; }
+  static __device__ __forceinline__ uint32_t bits(V x) { return __float_as_uint(x); }
+  static __device__ __forceinline__ V neg(V x) { return 0.0f - x; }
+  static __device__ __forceinline__ V max3(V a, V b, V c) {
+    float d;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+    return d;
+  }
+  static __device__ __forceinline__ V min3(V a, V b, V c) {
+    float d;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+    return d;
+  }
+  // sign bit set  <=>  max - min <= t_zc  (contrast test fails)
+  static __device__ __forceinline__ uint32_t cfail(const KParams &kp, int f, V mx, V mn) {
+    return __float_as_uint((mx - mn) - kp.tzc1f[f]);
+  }
+  // sign bit set  <=>  the standard-deviation test passes (reading R4)
+  static __device__ __forceinline__ uint32_t sdpass(const KParams &kp, int f, V A3, V A5, Q Q3, Q Q5) {
+    const uint32_t a3 = __float_as_uint(A3 + 8388608.0f) - 0x4B000000u;
+    const uint32_t a5 = __float_as_uint(A5 + 8388608.0f) - 0x4B000000u;
+    const uint32_t d3 = 9u * Q3 - a3 * a3;   // exact modulo 2^32, and D < 2^32
+    const uint32_t d5 = 25u * Q5 - a5 * a5;
+    const bool pass = d5 >= kp.ttmax[f] ? d3 >= kp.tt3[f] : d5 >= kp.tt5[f];
+    return pass ? 0x80000000u : 0u;
+  }
+  static __device__ __forceinline__ V fix(const KParams &kp, int f, V x) { return kp.fixzero[f] ? x + 0.0f : x; }
+};
+
+// Integer path: any uint16 value (|L| < 2^30 by the plan's range check).
+template <>
+struct Ar<true> {
+  using V = int32_t;
+  using Q = uint64_t;
+  static __device__ __forceinline__ V cvt(uint32_t u) { return static_cast<int32_t>(u); }
+  static __device__ __forceinline__ Q sq(uint32_t u) { return static_cast<uint64_t>(u) * u; }
+  static __device__ __forceinline__ V w(const KParams &kp, int f, int c) { return kp.ring[f][c]; }
+  static __device__ __forceinline__ uint32_t bits(V x) { return static_cast<uint32_t>(x); }
+  static __device__ __forceinline__ V neg(V x) { return -x; }
+  static __device__ __forceinline__ V max3(V a, V b, V c) { return max(max(a, b), c); }
+  static __device__ __forceinline__ V min3(V a, V b, V c) { return min(min(a, b), c); }
+  static __device__ __forceinline__ uint32_t cfail(const KParams &kp, int f, V mx, V mn) {
+    return static_cast<uint32_t>(mx - mn) - static_cast<uint32_t>(kp.tzc[f]) - 1u;
+  }
+  static __device__ __forceinline__ uint32_t sdpass(const KParams &kp, int f, V A3, V A5, Q Q3, Q Q5) {
+    const int64_t d3 = 9 * static_cast<int64_t>(Q3) - static_cast<int64_t>(A3) * A3;
+    const int64_t d5 = 25 * static_cast<int64_t>(Q5) - static_cast<int64_t>(A5) * A5;
+    const bool pass = d5 > kp.tsdmax[f] ? d3 > kp.tsd3[f] : d5 > kp.tsd5[f];
+    return pass ? 0x80000000u : 0u;
+  }
+  static __device__ __forceinline__ V fix(const KParams &, int, V x) { return x; }
+};
+
+template <typename T, bool kInt>
+struct Strip {
+  using A = Ar<kInt>;
+  using V = typename A::V;
+  using Q = typename A::Q;
+
+  const ImageView &v;
+  const KParams &kp;
+  int64_t X0, Y0, Y1, xs, W, H;
+  int lane;
+  bool check, border, vload, vstore;
+  int bl_lane, bl_slot, br_lane, br_slot;
+  uint32_t outmask_l, outmask_r;  // this lane's slots left of / right of the image (MJ0 << j)
+
+  V f_[8][4], h1_[8][4], h2_[8][4];
+  Q c3_[8][4], c5_[8][4];
+  V L_[2][8][4];
+  V LW_[2][8], LE_[2][8];
+  uint32_t S_[2][8][4];
+  uint32_t raw_[8][2];
+  uint32_t vmax_;
+  uint32_t acc_[12];
+  // Words of earlier blocks, touched once per 8 rows, live in shared memory:
+  // kBlk.. = previous block (12 words), kPrev.. = neg / pos / sS of the block
+  // before it (6), kMA / kMB = mask words of the two previous blocks.
+  uint32_t (*sw_)[32];
+  static constexpr int kBlk = 0, kPneg = 12, kPpos = 14, kPsS = 16, kMA = 18, kMB = 19, kWords = 20;
+  __device__ __forceinline__ uint32_t &blk(int i) { return sw_[kBlk + i][lane]; }
+
+  __device__ Strip(const ImageView &v_, const KParams &kp_, int64_t x0, int64_t y0, int64_t y1,
+                   uint32_t (*words)[32])
+      : v(v_), kp(kp_), X0(x0), Y0(y0), Y1(y1), sw_(words) {
+    lane = threadIdx.x & 31;
+    W = v.width;
+    H = v.height;
+    xs = X0 - kLeftHalo;
+    check = !kInt && kp.fbound < (sizeof(T) == 1 ? 255 : 65535);
+    border = xs < 0 || xs + 128 > W;
+    const uintptr_t base = reinterpret_cast<uintptr_t>(v.img);
+    vload = (base % (4 * sizeof(T)) == 0) && (v.pitch % (4 * sizeof(T)) == 0) && (xs % 4 == 0);
+    vstore = (reinterpret_cast<uintptr_t>(v.out) % 4 == 0) && (v.out_pitch % 4 == 0) && (xs % 4 == 0);
+    const int64_t bl = -xs, br = W - 1 - xs;  // window columns of image columns 0 and W-1
+    bl_lane = bl > 0 ? static_cast<int>(bl >> 2) : 0;
+    bl_slot = bl > 0 ? static_cast<int>(bl & 3) : 0;
+    br_lane = br < 127 ? static_cast<int>((br < 0 ? 0 : br) >> 2) : 31;
+    br_slot = br < 127 ? static_cast<int>((br < 0 ? 0 : br) & 3) : 3;
+    outmask_l = outmask_r = 0;
+    for (int j = 0; j < 4; ++j) {
+      const int64_t xg = xs + 4 * lane + j;
+      if (xg < 0) outmask_l |= MJ0 << j;
+      if (xg >= W) outmask_r |= MJ0 << j;
+    }
+    vmax_ = 0;
+    for (int i = 0; i < 12; ++i) acc_[i] = 0;
+    for (int i = 0; i < kWords; ++i) sw_[i][lane] = 0;
+#pragma unroll
+    for (int s = 0; s < 8; ++s) {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        f_[s][j] = h1_[s][j] = h2_[s][j] = V(0);
+        c3_[s][j] = c5_[s][j] = Q(0);
+        L_[0][s][j] = L_[1][s][j] = V(0);
+        S_[0][s][j] = S_[1][s][j] = 0;
+      }
+      LW_[0][s] = LW_[1][s] = LE_[0][s] = LE_[1][s] = V(0);
+    }
+  }
+
+  // Row t of the image (clamped) into raw slot S, as two words of 16-bit pairs.
+  template <int S>
+  __device__ __forceinline__ void load_row(int64_t t) {
+    // rows outside the image clamp to it (reading R2); rows outside the buffer
+    // (a row band) clamp to the buffer: they feed only rows that are not stored
+    const int64_t lo = v.row0 > 0 ? v.row0 : 0, hi = (v.row_lim < H ? v.row_lim : H) - 1;
+    const int64_t yr = (t < lo ? lo : (t > hi ? hi : t)) - v.row0;
+    const unsigned char *row = static_cast<const unsigned char *>(v.img) + yr * v.pitch;
+    const int64_t x = xs + 4 * lane;
+    if (vload && x >= 0 && x + 3 < W) {
+      if constexpr (sizeof(T) == 2) {
+        const uint2 q = __ldg(reinterpret_cast<const uint2 *>(row + 2 * x));
+        raw_[S][0] = q.x;
+        raw_[S][1] = q.y;
+      } else {
+        const uint32_t q = __ldg(reinterpret_cast<const uint32_t *>(row + x));
+        raw_[S][0] = __byte_perm(q, 0, 0x4140);
+        raw_[S][1] = __byte_perm(q, 0, 0x4342);
+      }
+    } else {
+      uint32_t u[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int64_t xc = x + j < 0 ? 0 : (x + j >= W ? W - 1 : x + j);
+        u[j] = static_cast<uint32_t>(__ldg(reinterpret_cast<const T *>(row) + xc));
+      }
+      raw_[S][0] = u[0] | (u[1] << 16);
+      raw_[S][1] = u[2] | (u[3] << 16);
+    }
+  }
+
+  // Replace the values of window columns outside the image by the value of the
+  // nearest image column (reading R2 for a stage array).
+  __device__ __forceinline__ void fix_cols(V x[4]) {
+    const V sl = bl_slot == 0 ? x[0] : bl_slot == 1 ? x[1] : bl_slot == 2 ? x[2] : x[3];
+    const V sr = br_slot == 0 ? x[0] : br_slot == 1 ? x[1] : br_slot == 2 ? x[2] : x[3];
+    const V lv = __shfl_sync(kFull, sl, bl_lane);
+    const V rv = __shfl_sync(kFull, sr, br_lane);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      if (outmask_l & (MJ0 << j)) x[j] = lv;
+      if (outmask_r & (MJ0 << j)) x[j] = rv;
+    }
+  }
+
+  // Same for a mask word: columns outside the image take the border column's bits.
+  __device__ __forceinline__ uint32_t fix_cols_bits(uint32_t m) {
+    const uint32_t ml = __shfl_sync(kFull, m, bl_lane);
+    const uint32_t mr = __shfl_sync(kFull, m, br_lane);
+    const uint32_t repl = ((ml >> bl_slot) & MJ0) * 0xFu;
+    const uint32_t repr = ((mr >> br_slot) & MJ0) * 0xFu;
+    m = (m & ~outmask_l) | (repl & outmask_l);
+    m = (m & ~outmask_r) | (repr & outmask_r);
+    return m;
+  }
+
+  template <int S, bool kL, bool kPack>
+  __device__ __forceinline__ void step(int64_t t) {
+    load_row<(S + 2) & 7>(t + 2);
+    const uint32_t w0 = raw_[S][0], w1v = raw_[S][1];
+    if (check) vmax_ = __vmaxu2(vmax_, __vmaxu2(w0, w1v));
+    const uint32_t hl = __shfl_up_sync(kFull, w1v, 1);
+    const uint32_t hr = __shfl_down_sync(kFull, w0, 1);
+    const uint32_t u[8] = {hl & 0xFFFFu, hl >> 16, w0 & 0xFFFFu, w0 >> 16,
+                           w1v & 0xFFFFu, w1v >> 16, hr & 0xFFFFu, hr >> 16};
+    V fv[8];
+    Q sq[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      fv[k] = A::cvt(u[k]);
+      sq[k] = A::sq(u[k]);
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      f_[S][j] = fv[j + 2];
+      h1_[S][j] = fv[j + 1] + fv[j + 3];
+      h2_[S][j] = fv[j] + fv[j + 4];
+      const Q c3 = sq[j + 1] + sq[j + 2] + sq[j + 3];
+      c3_[S][j] = c3;
+      c5_[S][j] = c3 + sq[j] + sq[j + 4];
+    }
+    if constexpr (kL) centre<S>(t - 2);
+    if constexpr (kPack) pack<S>();
+  }
+
+  // LoG responses and the standard-deviation test for the centre row c = t - 2.
+  template <int S>
+  __device__ __forceinline__ void centre(int64_t c) {
+    constexpr int c0 = (S + 6) & 7, m1 = (S + 5) & 7, p1 = (S + 7) & 7, m2 = (S + 4) & 7, p2 = S;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const V R0 = f_[c0][j];
+      const V R1 = h1_[c0][j] + (f_[m1][j] + f_[p1][j]);
+      const V R2 = h1_[m1][j] + h1_[p1][j];
+      const V R4 = h2_[c0][j] + (f_[m2][j] + f_[p2][j]);
+      const V R5 = (h2_[m1][j] + h2_[p1][j]) + (h1_[m2][j] + h1_[p2][j]);
+      const V R8 = h2_[m2][j] + h2_[p2][j];
+#pragma unroll
+      for (int f = 0; f < 2; ++f) {
+        V l = A::w(kp, f, 0) * R0;
+        l = l + A::w(kp, f, 1) * R1;
+        l = l + A::w(kp, f, 2) * R2;
+        l = l + A::w(kp, f, 3) * R4;
+        l = l + A::w(kp, f, 4) * R5;
+        l = l + A::w(kp, f, 5) * R8;  // positive outer weight last: no -0 (else fix)
+        L_[f][c0][j] = A::fix(kp, f, l);
+      }
+      const V A3 = R0 + R1 + R2;
+      const V A5 = A3 + R4 + R5 + R8;
+      const Q Q3 = c3_[m1][j] + c3_[c0][j] + c3_[p1][j];
+      const Q Q5 = c5_[m2][j] + c5_[m1][j] + c5_[c0][j] + c5_[p1][j] + c5_[p2][j];
+      S_[0][c0][j] = A::sdpass(kp, 0, A3, A5, Q3, Q5);
+      if (!kp.sd_same) S_[1][c0][j] = A::sdpass(kp, 1, A3, A5, Q3, Q5);
+    }
+    // replicated borders for the L stage (reading R2)
+    if (c >= H) {
+#pragma unroll
+      for (int f = 0; f < 2; ++f)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) L_[f][c0][j] = L_[f][m1][j];
+    }
+    if (border) {
+      fix_cols(L_[0][c0]);
+      fix_cols(L_[1][c0]);
+    }
+    if (c == 0) {
+#pragma unroll
+      for (int f = 0; f < 2; ++f)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) L_[f][m1][j] = L_[f][c0][j];
+    }
+#pragma unroll
+    for (int f = 0; f < 2; ++f) {
+      LW_[f][c0] = __shfl_up_sync(kFull, L_[f][c0][3], 1);
+      LE_[f][c0] = __shfl_down_sync(kFull, L_[f][c0][0], 1);
+    }
+  }
+
+  // Bits of row c' = t - 3 (its south neighbour row t - 2 is now known).
+  template <int S>
+  __device__ __forceinline__ void pack() {
+    constexpr int r = (S + 5) & 7, rn = (S + 4) & 7, rs = (S + 6) & 7;
+#pragma unroll
+    for (int f = 0; f < 2; ++f) {
+#pragma unroll
+      for (int jj = 0; jj < 4; ++jj) {
+        const int j = 3 - jj;
+        const V Lc = L_[f][r][j], Ln = L_[f][rn][j], Ls = L_[f][rs][j];
+        const V Lw = j > 0 ? L_[f][r][j > 0 ? j - 1 : 0] : LW_[f][r];
+        const V Le = j < 3 ? L_[f][r][j < 3 ? j + 1 : 3] : LE_[f][r];
+        put(acc_[5 * f + 0], A::bits(Lc));
+        put(acc_[5 * f + 1], A::bits(A::neg(Lc)));
+        put(acc_[5 * f + 2], A::bits(Lc + Le));
+        put(acc_[5 * f + 3], A::bits(Lc + Ls));
+        const V mx = A::max3(A::max3(Lw, Lc, Le), Ln, Ls);
+        const V mn = A::min3(A::min3(Lw, Lc, Le), Ln, Ls);
+        put(acc_[5 * f + 4], A::cfail(kp, f, mx, mn));
+      }
+    }
+#pragma unroll
+    for (int jj = 0; jj < 4; ++jj) put(acc_[10], S_[0][r][3 - jj]);
+    if (!kp.sd_same) {
+#pragma unroll
+      for (int jj = 0; jj < 4; ++jj) put(acc_[11], S_[1][r][3 - jj]);
+    }
+  }
+
+  // Block b = g - 1 (words blk_): zero crossings, extraction, OR (the mask M).
+  __device__ __forceinline__ uint32_t mask_block(int64_t b) {
+    uint32_t m = 0;
+#pragma unroll
+    for (int f = 0; f < 2; ++f) {
+      const uint32_t neg = blk(5 * f), pos = blk(5 * f + 1), sE = blk(5 * f + 2), sS = blk(5 * f + 3);
+      const uint32_t cf = blk(5 * f + 4);
+      const uint32_t negP = __shfl_up_sync(kFull, neg, 1), negX = __shfl_down_sync(kFull, neg, 1);
+      const uint32_t posP = __shfl_up_sync(kFull, pos, 1), posX = __shfl_down_sync(kFull, pos, 1);
+      const uint32_t sEP = __shfl_up_sync(kFull, sE, 1);
+      const uint32_t nE = e1(neg, negX), pE = e1(pos, posX), nW = w1(neg, negP), pW = w1(pos, posP);
+      const uint32_t nN = n1(neg, sw_[kPneg + f][lane]), pN = n1(pos, sw_[kPpos + f][lane]);
+      const uint32_t nS = s1(neg, acc_[5 * f]), pS = s1(pos, acc_[5 * f + 1]);
+      const uint32_t sW = w1(sE, sEP), sN = n1(sS, sw_[kPsS + f][lane]);
+      // crossing with each neighbour, and losing it: the pixel wins an edge iff
+      // it is the negative one XOR the edge sum is negative (reading R3)
+      const uint32_t xE = (neg & pE) | (pos & nE), xW = (neg & pW) | (pos & nW);
+      const uint32_t xN = (neg & pN) | (pos & nN), xS = (neg & pS) | (pos & nS);
+      const uint32_t lE = xE & ~(neg ^ sE), lW = xW & ~(neg ^ sW);
+      const uint32_t lN = xN & ~(neg ^ sN), lS = xS & ~(neg ^ sS);
+      const uint32_t znz = (xE | xW | xN | xS) & ~(lE | lW | lN | lS);
+      const uint32_t z0 = ~(neg | pos) & ((nW & pE) | (pW & nE) | (nN & pS) | (pN & nS));
+      const uint32_t sd = kp.sd_same ? blk(10) : blk(10 + f);
+      m |= (znz | z0) & ~cf & sd;
+    }
+    // replicated borders for the mask (reading R2)
+    const int64_t r0 = Y0 - 3 + 8 * b;  // image row of bit-row 0
+    if (r0 < 0) {  // top: rows -3..-1 take row 0 (bit-row 3)
+      const uint32_t nib = (m >> 16) & 0xFu;
+      m = (m & 0x000FFFFFu) | (nib << 20) | (nib << 24) | (nib << 28);
+    }
+    if (r0 + 7 >= H) {  // bottom: rows >= H take row H - 1
+      const int64_t rH = H - 1 - r0;
+      if (rH >= 0) {
+        const uint32_t keep = 0xFFFFFFFFu << (4 * (7 - rH));
+        const uint32_t nib = (m >> (28 - 4 * rH)) & 0xFu;
+        m = (m & keep) | ((nib * 0x11111111u) & ~keep);
+      } else {
+        m = (sw_[kMA][lane] & 0xFu) * 0x11111111u;
+      }
+    }
+    if (border) m = fix_cols_bits(m);
+    return m;
+  }
+
+  // Hybrid median of block own (prev / next: the blocks above / below) and
+  // the store of its output rows.
+  __device__ __forceinline__ void median_store(int64_t b, uint32_t prev, uint32_t own, uint32_t next) {
+    uint32_t h = own;
+    const int k = kp.nhmf ? kp.hmf[0] : 0;
+    if (k) {
+      const uint32_t oP = __shfl_up_sync(kFull, own, 1), oX = __shfl_down_sync(kFull, own, 1);
+      const uint32_t pP = __shfl_up_sync(kFull, prev, 1), pX = __shfl_down_sync(kFull, prev, 1);
+      const uint32_t xP = __shfl_up_sync(kFull, next, 1), xX = __shfl_down_sync(kFull, next, 1);
+      const uint32_t E1o = e1(own, oX), W1o = w1(own, oP), E1p = e1(prev, pX), W1p = w1(prev, pP);
+      const uint32_t E1n = e1(next, xX), W1n = w1(next, xP);
+      if (k == 5) {
+        const uint32_t E2o = e2(own, oX), W2o = w2(own, oP), E2p = e2(prev, pX), W2p = w2(prev, pP);
+        const uint32_t E2n = e2(next, xX), W2n = w2(next, xP);
+        const uint32_t plus[9] = {own, E1o, W1o, E2o, W2o, n1(own, prev), s1(own, next), n2(own, prev), s2(own, next)};
+        const uint32_t cross[9] = {own, n1(E1o, E1p), n1(W1o, W1p), s1(E1o, E1n), s1(W1o, W1n),
+                                   n2(E2o, E2p), n2(W2o, W2p), s2(E2o, E2n), s2(W2o, W2n)};
+        h = maj3(maj9(plus), maj9(cross), own);
+      } else {
+        const uint32_t plus[5] = {own, E1o, W1o, n1(own, prev), s1(own, next)};
+        const uint32_t cross[5] = {own, n1(E1o, E1p), n1(W1o, W1p), s1(E1o, E1n), s1(W1o, W1n)};
+        h = maj3(maj5(plus), maj5(cross), own);
+      }
+    }
+    const int64_t x = xs + 4 * lane;
+    const bool lane_out = lane >= 2 && lane < 30 && x < W;
+    if (!lane_out) return;
+    const bool full = vstore && x + 3 < W;
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      const int64_t y = Y0 - 3 + 8 * b + r;
+      if (y < Y0 || y >= Y1) continue;
+      const uint32_t nib = (h >> (28 - 4 * r)) & 0xFu;
+      const uint32_t bytes = (nib * 0x00204081u) & 0x01010101u;
+      uint8_t *dst = v.out + (y - v.y_begin) * v.out_pitch + x;
+      if (full) {
+        *reinterpret_cast<uint32_t *>(dst) = bytes;
+      } else {
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          if (x + j < W) dst[j] = static_cast<uint8_t>((bytes >> (8 * j)) & 1u);
+      }
+    }
+  }
+
+  // End of the 8 steps of group g: block g is packed in acc_.
+  __device__ __forceinline__ bool end_group(int64_t g) {
+    if (check) {
+      const uint32_t m = max(vmax_ & 0xFFFFu, vmax_ >> 16);
+      if (__any_sync(kFull, m > static_cast<uint32_t>(kp.fbound))) return false;
+    }
+    uint32_t m = 0;
+    if (g >= 1) m = mask_block(g - 1);
+    if (g >= 2) median_store(g - 2, sw_[kMB][lane], sw_[kMA][lane], m);
+    sw_[kMB][lane] = sw_[kMA][lane];
+    sw_[kMA][lane] = m;
+#pragma unroll
+    for (int f = 0; f < 2; ++f) {
+      sw_[kPneg + f][lane] = blk(5 * f);
+      sw_[kPpos + f][lane] = blk(5 * f + 1);
+      sw_[kPsS + f][lane] = blk(5 * f + 3);
+    }
+#pragma unroll
+    for (int i = 0; i < 12; ++i) blk(i) = acc_[i];
+    return true;
+  }
+
+  template <int S>
+  __device__ __forceinline__ void group_steps(int64_t t0) {
+    step<S, true, true>(t0 + S);
+    if constexpr (S < 7) group_steps<S + 1>(t0);
+  }
+
+  __device__ bool run() {
+    // slot of row t = (t - Y0) & 7
+    load_row<3>(Y0 - 5);
+    load_row<4>(Y0 - 4);
+    step<3, false, false>(Y0 - 5);
+    step<4, false, false>(Y0 - 4);
+    step<5, false, false>(Y0 - 3);
+    step<6, false, false>(Y0 - 2);
+    step<7, true, false>(Y0 - 1);
+    // block b covers rows [Y0 - 3 + 8b, Y0 + 5 + 8b); the median of block b is
+    // stored at the end of group b + 2
+    const int64_t bmax = (Y1 - Y0 + 2) / 8;
+    const int64_t groups = bmax + 3;
+    for (int64_t g = 0; g < groups; ++g) {
+      group_steps<0>(Y0 + 8 * g);
+      if (!end_group(g)) return false;
+    }
+    return true;
+  }
+};
+
+}  // namespace st
+
+// Work units: output columns [112 ux, 112 ux + 112), rows [y_begin + uh uy,
+// + uh) of the view, computed by the calling warp.
+//
+// fast_unit runs the FP32 path.  A strip that meets a value above
+// KParams::fbound stops before storing anything that depends on it and marks
+// its first output byte with kRedo (masks are otherwise 0 or 1);
+// fast_unit_redo, launched afterwards on the same stream, recomputes exactly
+// the marked strips on the integer path (every strip when fbound < 0).  The
+// two paths are separate kernels so the rare integer path does not raise the
+// register allocation of the FP32 one.
+constexpr uint8_t kRedo = 0xFF;
+
+__device__ __forceinline__ uint8_t *unit_marker(const ImageView &v, int64_t ux, int64_t uy, int uh) {
+  return v.out + (uy * uh) * v.out_pitch + ux * st::kOutCols;
 }
 
 template <typename T>
-__device__ void fast_unit(const ImageView &v, const KParams &kp, int64_t ux, int64_t uy, int uw, int uh,
-                          unsigned char *smem) {
-  gen::general_tile<T>(v, kp, ux * gen::TW, uy * gen::TH, smem);
+__device__ __forceinline__ void fast_unit(const ImageView &v, const KParams &kp, int64_t ux, int64_t uy, int,
+                                          int uh, unsigned char *) {
+  if (kp.fbound < 0) return;
+  __shared__ uint32_t words[kWarpsPerCta][st::Strip<T, false>::kWords][32];
+  const int64_t X0 = ux * st::kOutCols;
+  const int64_t Y0 = v.y_begin + uy * uh;
+  const int64_t Y1 = Y0 + uh < v.y_end ? Y0 + uh : v.y_end;
+  st::Strip<T, false> s(v, kp, X0, Y0, Y1, words[(threadIdx.x >> 5) % kWarpsPerCta]);
+  if (!s.run() && (threadIdx.x & 31) == 0) *unit_marker(v, ux, uy, uh) = kRedo;
+}
+
+template <typename T>
+__device__ __forceinline__ void fast_unit_redo(const ImageView &v, const KParams &kp, int64_t ux, int64_t uy,
+                                               int, int uh, unsigned char *) {
+  if (kp.fbound >= 0) {
+    uint8_t mark = 0;
+    if ((threadIdx.x & 31) == 0) mark = *unit_marker(v, ux, uy, uh);
+    if (__shfl_sync(st::kFull, mark, 0) != kRedo) return;
+  }
+  __shared__ uint32_t words[kWarpsPerCta][st::Strip<T, true>::kWords][32];
+  const int64_t X0 = ux * st::kOutCols;
+  const int64_t Y0 = v.y_begin + uy * uh;
+  const int64_t Y1 = Y0 + uh < v.y_end ? Y0 + uh : v.y_end;
+  st::Strip<T, true> s(v, kp, X0, Y0, Y1, words[(threadIdx.x >> 5) % kWarpsPerCta]);
+  s.run();
 }
 
 }  // namespace fx
