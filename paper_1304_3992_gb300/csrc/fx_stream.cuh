@@ -196,6 +196,18 @@ struct Strip {
     border = xs < 0 || xs + 128 > W;
     const uintptr_t base = reinterpret_cast<uintptr_t>(v.img);
     vload = (base % (4 * sizeof(T)) == 0) && (v.pitch % (4 * sizeof(T)) == 0) && (xs % 4 == 0);
+    {
+      const int64_t lo = v.row0 > 0 ? v.row0 : 0, hi = (v.row_lim < H ? v.row_lim : H) - 1;
+      rlo = static_cast<int32_t>(lo - Y0);
+      Hrel = static_cast<int32_t>(H - Y0);
+      Y0rel = static_cast<int32_t>(Y0 < (1 << 30) ? Y0 : (1 << 30));
+      rhi = static_cast<int32_t>(hi - Y0);
+      const int64_t x = xs + 4 * lane;
+      cload = vload && x >= 0 && x + 3 < W;
+      for (int j = 0; j < 4; ++j) xcl[j] = static_cast<int32_t>(x + j < 0 ? 0 : (x + j >= W ? W - 1 : x + j));
+      rowY0 = static_cast<const unsigned char *>(v.img) + (Y0 - v.row0) * v.pitch +
+              (cload ? x * static_cast<int64_t>(sizeof(T)) : 0);
+    }
     vstore = (reinterpret_cast<uintptr_t>(v.out) % 4 == 0) && (v.out_pitch % 4 == 0) && (xs % 4 == 0);
     const int64_t bl = -xs, br = W - 1 - xs;  // window columns of image columns 0 and W-1
     bl_lane = bl > 0 ? static_cast<int>(bl >> 2) : 0;
@@ -225,31 +237,35 @@ struct Strip {
   }
 
   // Row t of the image (clamped) into raw slot S, as two words of 16-bit pairs.
+  // Row t of the image (clamped) into raw slot S, as two words of 16-bit pairs.
+  // Rows outside the image clamp to it (reading R2); rows outside the buffer
+  // (a row band) clamp to the buffer: they feed only rows that are not stored.
+  // rlo / rhi: first / last loadable row relative to Y0; colp: this lane's
+  // first column in row Y0 (or, with cload, the row base).
+  int32_t rlo, rhi;
+  int32_t Hrel, Y0rel;  // H - Y0 and Y0 (clamped to int32 range)
+  const unsigned char *rowY0;
+  bool cload;  // this lane's 4 columns are inside the image and aligned
+  int32_t xcl[4];  // clamped columns (only when !cload)
+
   template <int S>
-  __device__ __forceinline__ void load_row(int64_t t) {
-    // rows outside the image clamp to it (reading R2); rows outside the buffer
-    // (a row band) clamp to the buffer: they feed only rows that are not stored
-    const int64_t lo = v.row0 > 0 ? v.row0 : 0, hi = (v.row_lim < H ? v.row_lim : H) - 1;
-    const int64_t yr = (t < lo ? lo : (t > hi ? hi : t)) - v.row0;
-    const unsigned char *row = static_cast<const unsigned char *>(v.img) + yr * v.pitch;
-    const int64_t x = xs + 4 * lane;
-    if (vload && x >= 0 && x + 3 < W) {
+  __device__ __forceinline__ void load_row(int32_t tr) {  // tr = t - Y0
+    const int32_t yr = tr < rlo ? rlo : (tr > rhi ? rhi : tr);
+    const unsigned char *row = rowY0 + static_cast<int64_t>(yr) * v.pitch;
+    if (cload) {
       if constexpr (sizeof(T) == 2) {
-        const uint2 q = __ldg(reinterpret_cast<const uint2 *>(row + 2 * x));
+        const uint2 q = __ldg(reinterpret_cast<const uint2 *>(row));
         raw_[S][0] = q.x;
         raw_[S][1] = q.y;
       } else {
-        const uint32_t q = __ldg(reinterpret_cast<const uint32_t *>(row + x));
+        const uint32_t q = __ldg(reinterpret_cast<const uint32_t *>(row));
         raw_[S][0] = __byte_perm(q, 0, 0x4140);
         raw_[S][1] = __byte_perm(q, 0, 0x4342);
       }
     } else {
       uint32_t u[4];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const int64_t xc = x + j < 0 ? 0 : (x + j >= W ? W - 1 : x + j);
-        u[j] = static_cast<uint32_t>(__ldg(reinterpret_cast<const T *>(row) + xc));
-      }
+      for (int j = 0; j < 4; ++j) u[j] = static_cast<uint32_t>(__ldg(reinterpret_cast<const T *>(row) + xcl[j]));
       raw_[S][0] = u[0] | (u[1] << 16);
       raw_[S][1] = u[2] | (u[3] << 16);
     }
@@ -281,7 +297,7 @@ struct Strip {
   }
 
   template <int S, bool kL, bool kPack>
-  __device__ __forceinline__ void step(int64_t t) {
+  __device__ __forceinline__ void step(int32_t t) {  // t relative to Y0
     load_row<(S + 2) & 7>(t + 2);
     const uint32_t w0 = raw_[S][0], w1v = raw_[S][1];
     if (check) vmax_ = __vmaxu2(vmax_, __vmaxu2(w0, w1v));
@@ -311,7 +327,7 @@ struct Strip {
 
   // LoG responses and the standard-deviation test for the centre row c = t - 2.
   template <int S>
-  __device__ __forceinline__ void centre(int64_t c) {
+  __device__ __forceinline__ void centre(int32_t c) {  // c relative to Y0
     constexpr int c0 = (S + 6) & 7, m1 = (S + 5) & 7, p1 = (S + 7) & 7, m2 = (S + 4) & 7, p2 = S;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
@@ -339,7 +355,7 @@ struct Strip {
       if (!kp.sd_same) S_[1][c0][j] = A::sdpass(kp, 1, A3, A5, Q3, Q5);
     }
     // replicated borders for the L stage (reading R2)
-    if (c >= H) {
+    if (c >= Hrel) {
 #pragma unroll
       for (int f = 0; f < 2; ++f)
 #pragma unroll
@@ -349,7 +365,7 @@ struct Strip {
       fix_cols(L_[0][c0]);
       fix_cols(L_[1][c0]);
     }
-    if (c == 0) {
+    if (c == -Y0rel) {
 #pragma unroll
       for (int f = 0; f < 2; ++f)
 #pragma unroll
@@ -504,26 +520,22 @@ struct Strip {
   }
 
   template <int S>
-  __device__ __forceinline__ void group_steps(int64_t t0) {
+  __device__ __forceinline__ void group_steps(int32_t t0) {  // relative to Y0
     step<S, true, true>(t0 + S);
     if constexpr (S < 7) group_steps<S + 1>(t0);
   }
 
   __device__ bool run() {
-    // slot of row t = (t - Y0) & 7
-    load_row<3>(Y0 - 5);
-    load_row<4>(Y0 - 4);
-    step<3, false, false>(Y0 - 5);
-    step<4, false, false>(Y0 - 4);
-    step<5, false, false>(Y0 - 3);
-    step<6, false, false>(Y0 - 2);
-    step<7, true, false>(Y0 - 1);
+    // slot of row t = (t - Y0) & 7.  Group -1 (rows Y0-8 .. Y0-1) fills the
+    // rings; it computes responses and bits of rows no output depends on.
+    load_row<0>(-8);
+    load_row<1>(-7);
     // block b covers rows [Y0 - 3 + 8b, Y0 + 5 + 8b); the median of block b is
     // stored at the end of group b + 2
-    const int64_t bmax = (Y1 - Y0 + 2) / 8;
-    const int64_t groups = bmax + 3;
-    for (int64_t g = 0; g < groups; ++g) {
-      group_steps<0>(Y0 + 8 * g);
+    const int32_t bmax = static_cast<int32_t>((Y1 - Y0 + 2) / 8);
+    const int32_t groups = bmax + 3;
+    for (int32_t g = -1; g < groups; ++g) {
+      group_steps<0>(8 * g);
       if (!end_group(g)) return false;
     }
     return true;
