@@ -170,12 +170,14 @@ struct Strip {
   int bl_lane, bl_slot, br_lane, br_slot;
   uint32_t outmask_l, outmask_r;  // this lane's slots left of / right of the image (MJ0 << j)
 
-  V f_[8][4], h1_[8][4], h2_[8][4];
-  Q c3_[8][4], c5_[8][4];
-  V L_[2][8][4];
-  V LW_[2][8], LE_[2][8];
-  uint32_t S_[2][8][4];
-  uint32_t raw_[8][2];
+  // Rings of period 4 (slot of row t = t & 3).  The row four steps back is
+  // read before the newest row overwrites its slot.
+  V f_[4][4], h1_[4][4], h2_[4][4];
+  Q c3_[4][4], c5_[4][4];
+  V L_[2][4][4];
+  V LW_[2][4], LE_[2][4];
+  uint32_t S_[2][4][4];
+  uint32_t raw_[4][2];
   uint32_t vmax_;
   uint32_t acc_[12];
   // Words of earlier blocks, touched once per 8 rows, live in shared memory:
@@ -224,7 +226,7 @@ struct Strip {
     for (int i = 0; i < 12; ++i) acc_[i] = 0;
     for (int i = 0; i < kWords; ++i) sw_[i][lane] = 0;
 #pragma unroll
-    for (int s = 0; s < 8; ++s) {
+    for (int s = 0; s < 4; ++s) {
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
         f_[s][j] = h1_[s][j] = h2_[s][j] = V(0);
@@ -297,8 +299,8 @@ struct Strip {
   }
 
   template <int S, bool kL, bool kPack>
-  __device__ __forceinline__ void step(int32_t t) {  // t relative to Y0
-    load_row<(S + 2) & 7>(t + 2);
+  __device__ __forceinline__ void step(int32_t t) {  // t relative to Y0, S = t & 3
+    load_row<(S + 2) & 3>(t + 2);
     const uint32_t w0 = raw_[S][0], w1v = raw_[S][1];
     if (check) vmax_ = __vmaxu2(vmax_, __vmaxu2(w0, w1v));
     const uint32_t hl = __shfl_up_sync(kFull, w1v, 1);
@@ -312,31 +314,42 @@ struct Strip {
       fv[k] = A::cvt(u[k]);
       sq[k] = A::sq(u[k]);
     }
+    V fn[4], h1n[4], h2n[4];
+    Q c3n[4], c5n[4];
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-      f_[S][j] = fv[j + 2];
-      h1_[S][j] = fv[j + 1] + fv[j + 3];
-      h2_[S][j] = fv[j] + fv[j + 4];
-      const Q c3 = sq[j + 1] + sq[j + 2] + sq[j + 3];
-      c3_[S][j] = c3;
-      c5_[S][j] = c3 + sq[j] + sq[j + 4];
+      fn[j] = fv[j + 2];
+      h1n[j] = fv[j + 1] + fv[j + 3];
+      h2n[j] = fv[j] + fv[j + 4];
+      c3n[j] = sq[j + 1] + sq[j + 2] + sq[j + 3];
+      c5n[j] = c3n[j] + sq[j] + sq[j + 4];
     }
-    if constexpr (kL) centre<S>(t - 2);
+    if constexpr (kL) centre<S>(t - 2, fn, h1n, h2n, c5n);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      f_[S][j] = fn[j];
+      h1_[S][j] = h1n[j];
+      h2_[S][j] = h2n[j];
+      c3_[S][j] = c3n[j];
+      c5_[S][j] = c5n[j];
+    }
     if constexpr (kPack) pack<S>();
   }
 
-  // LoG responses and the standard-deviation test for the centre row c = t - 2.
+  // LoG responses and the standard-deviation test for the centre row c = t - 2
+  // (row t arrives in fn / h1n / h2n / c5n; slot S still holds row t - 4).
   template <int S>
-  __device__ __forceinline__ void centre(int32_t c) {  // c relative to Y0
-    constexpr int c0 = (S + 6) & 7, m1 = (S + 5) & 7, p1 = (S + 7) & 7, m2 = (S + 4) & 7, p2 = S;
+  __device__ __forceinline__ void centre(int32_t c, const V fn[4], const V h1n[4], const V h2n[4],
+                                         const Q c5n[4]) {
+    constexpr int c0 = (S + 2) & 3, m1 = (S + 1) & 3, p1 = (S + 3) & 3, m2 = S;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const V R0 = f_[c0][j];
       const V R1 = h1_[c0][j] + (f_[m1][j] + f_[p1][j]);
       const V R2 = h1_[m1][j] + h1_[p1][j];
-      const V R4 = h2_[c0][j] + (f_[m2][j] + f_[p2][j]);
-      const V R5 = (h2_[m1][j] + h2_[p1][j]) + (h1_[m2][j] + h1_[p2][j]);
-      const V R8 = h2_[m2][j] + h2_[p2][j];
+      const V R4 = h2_[c0][j] + (f_[m2][j] + fn[j]);
+      const V R5 = (h2_[m1][j] + h2_[p1][j]) + (h1_[m2][j] + h1n[j]);
+      const V R8 = h2_[m2][j] + h2n[j];
 #pragma unroll
       for (int f = 0; f < 2; ++f) {
         V l = A::w(kp, f, 0) * R0;
@@ -350,7 +363,7 @@ struct Strip {
       const V A3 = R0 + R1 + R2;
       const V A5 = A3 + R4 + R5 + R8;
       const Q Q3 = c3_[m1][j] + c3_[c0][j] + c3_[p1][j];
-      const Q Q5 = c5_[m2][j] + c5_[m1][j] + c5_[c0][j] + c5_[p1][j] + c5_[p2][j];
+      const Q Q5 = c5_[m2][j] + c5_[m1][j] + c5_[c0][j] + c5_[p1][j] + c5n[j];
       S_[0][c0][j] = A::sdpass(kp, 0, A3, A5, Q3, Q5);
       if (!kp.sd_same) S_[1][c0][j] = A::sdpass(kp, 1, A3, A5, Q3, Q5);
     }
@@ -381,7 +394,7 @@ struct Strip {
   // Bits of row c' = t - 3 (its south neighbour row t - 2 is now known).
   template <int S>
   __device__ __forceinline__ void pack() {
-    constexpr int r = (S + 5) & 7, rn = (S + 4) & 7, rs = (S + 6) & 7;
+    constexpr int r = (S + 1) & 3, rn = S, rs = (S + 2) & 3;  // rows t-3, t-4, t-2
 #pragma unroll
     for (int f = 0; f < 2; ++f) {
 #pragma unroll
@@ -519,24 +532,25 @@ struct Strip {
     return true;
   }
 
-  template <int S>
-  __device__ __forceinline__ void group_steps(int32_t t0) {  // relative to Y0
-    step<S, true, true>(t0 + S);
-    if constexpr (S < 7) group_steps<S + 1>(t0);
+  __device__ __forceinline__ void four_steps(int32_t t0) {  // t0 = 4k relative to Y0
+    step<0, true, true>(t0);
+    step<1, true, true>(t0 + 1);
+    step<2, true, true>(t0 + 2);
+    step<3, true, true>(t0 + 3);
   }
 
   __device__ bool run() {
-    // slot of row t = (t - Y0) & 7.  Group -1 (rows Y0-8 .. Y0-1) fills the
-    // rings; it computes responses and bits of rows no output depends on.
+    // Rows Y0-8 .. Y0-1 (k = -2, -1) fill the rings; they compute responses and
+    // bits of rows no output depends on.  Bit blocks span 8 rows (two
+    // iterations); block b covers rows [Y0 - 3 + 8b, Y0 + 5 + 8b) and its
+    // median is stored at the end of block b + 2.
     load_row<0>(-8);
     load_row<1>(-7);
-    // block b covers rows [Y0 - 3 + 8b, Y0 + 5 + 8b); the median of block b is
-    // stored at the end of group b + 2
     const int32_t bmax = static_cast<int32_t>((Y1 - Y0 + 2) / 8);
-    const int32_t groups = bmax + 3;
-    for (int32_t g = -1; g < groups; ++g) {
-      group_steps<0>(8 * g);
-      if (!end_group(g)) return false;
+    const int32_t iters = 2 * (bmax + 3);
+    for (int32_t k = -2; k < iters; ++k) {
+      four_steps(4 * k);
+      if ((k & 1) && !end_group(k >> 1)) return false;
     }
     return true;
   }
