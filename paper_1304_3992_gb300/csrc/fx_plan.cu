@@ -476,8 +476,8 @@ fx_status fx_extract_host(fx_plan *p, const void *img_host, int64_t width, int64
   if (cudaSetDevice(p->device) != cudaSuccess) return FX_ERR_CUDA;
   const int64_t r = kp.r_in;
   const int64_t dpitch = (width * elem + 255) / 256 * 256;
-  // bands of ~64 MiB of input, at least 64 rows
-  int64_t band = std::max<int64_t>(64, (64LL << 20) / dpitch);
+  // bands of ~256 MiB of input (enough strips to fill the GPU), at least 64 rows
+  int64_t band = std::max<int64_t>(64, (256LL << 20) / dpitch);
   band = std::min(band, height);
   const int64_t in_rows = std::min(height, band + 2 * r);
   const size_t need_in = static_cast<size_t>(in_rows * dpitch);
