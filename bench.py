@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-vs-plain comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--side", type=int, default=SIDE, help="band side (default 16384)")
+    ap.add_argument("--serve-duration", type=float, default=10.0,
+                    help="seconds of the Poisson serving run (0 skips it; 60 is the full workload)")
     return ap.parse_args()
 
 
@@ -207,6 +209,24 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------ replicas
+
+def max_over_ranks(value: float, device) -> float:
+    """The slowest rank's time (replicas: every rank runs the same workload)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_gpx_s(px_per_step_per_rank: int, steps: int, elapsed_ms: float, world: int) -> float:
+    """Whole-job throughput: all ranks' pixels over the slowest rank's time."""
+    return world * px_per_step_per_rank * steps / (elapsed_ms * 1e-3) / 1e9
+
+
 # ------------------------------------------------------------------ main
 
 def main():
@@ -268,11 +288,8 @@ def main():
         barrier()
     elapsed_ms = e0.elapsed_time(e1)
     launch_ms = [launch_ev[k][2 * i].elapsed_time(launch_ev[k][2 * i + 1]) for k in range(K) for i in range(BANDS)]
-    if world > 1:
-        t = torch.tensor([elapsed_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
-    value = world * px_step * K / (elapsed_ms * 1e-3) / 1e9
+    elapsed_ms = max_over_ranks(elapsed_ms, dev)
+    value = aggregate_gpx_s(px_step, K, elapsed_ms, world)
 
     # ---- end to end through the C ABI on pinned host buffers
     h_in = [torch.from_numpy(b).pin_memory() for b in bands_np]
@@ -298,6 +315,11 @@ def main():
     if not args.no_batch:
         batched = bench_batched(fx, torch, dev, params, plan_cls=fx.Plan)
     plan.close()
+
+    # ---- continuous-batching server under a Poisson stream
+    serving = None
+    if args.serve_duration > 0:
+        serving = bench_serving(fx, torch, dev, params, bands_np[0], args.serve_duration)
 
     # ---- roofline of the fused kernel
     peak, peak_src, _ = peaks()
@@ -338,7 +360,7 @@ def main():
             "roofline": roof, "issue_roof": issue, "cpu_baseline": cpu, "e2e": e2e,
             # per band: the streaming kernel and the integer redo check (12-bit data
             # is within the FP32-exact bound, so the redo kernel only reads markers)
-            "gpu_launches": K * BANDS * 2, "clocks": clk, "batched": batched,
+            "gpu_launches": K * BANDS * 2, "clocks": clk, "batched": batched, "serving": serving,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -380,6 +402,44 @@ def bench_batched(fx, torch, dev, params, plan_cls):
     return {"scenes": 64, "pixels": px, "batched_gpx_s": px / t_batch / 1e6,
             "one_by_one_gpx_s": px / t_plain / 1e6, "speedup": t_plain / t_batch,
             "identical_output": bool(same), "tile": list(tuned)}
+
+
+def bench_serving(fx, torch, dev, params, master16, duration):
+    """Poisson stream (200 req/s) of single-band scenes with sides log-uniform in
+    [512, 16384] px, uint8/uint16 alternating, cropped from two 16384^2 masters
+    into a pool of 48 pinned requests; 40 GB HBM budget; masks released as soon
+    as they complete.  Every 50th served mask is compared byte for byte with a
+    lone fx_extract call on the same image."""
+    from gen import scenes
+    from paper_1304_3992_gb300.serve import Server, TorchBackend, run_stream
+    rng = np.random.default_rng(7)
+    side = master16.shape[0]
+    master8 = scenes.scene(side, side, seed=8, n_rects=int(40 * side * side / 512 ** 2), noise_sigma=4.0,
+                           impulse_frac=0.01, bits=8)
+    pool = []
+    for i in range(48):
+        h, w = (int(round(float(np.exp(rng.uniform(np.log(512), np.log(side)))))) for _ in range(2))
+        y0, x0 = int(rng.integers(0, side - h + 1)), int(rng.integers(0, side - w + 1))
+        src = master8 if i % 2 == 0 else master16
+        pool.append(torch.from_numpy(np.ascontiguousarray(src[y0:y0 + h, x0:x0 + w])).pin_memory().numpy())
+    be = TorchBackend(params, slots=2, max_images=64, device=dev.index or 0)
+    server = Server(be, budget_bytes=40 * 10**9, max_batch=64)
+    checks = {}
+
+    def keep(r):
+        if r.rid % 50 == 0:
+            checks[r.rid] = (r.image, r.dev["out"].cpu())
+
+    reqs = run_stream(server, pool, rate_hz=200.0, duration_s=duration, seed=7, on_done=keep)
+    st = server.stats()
+    same = all(torch.equal(fx.extract(torch.from_numpy(im).to(dev), params).cpu(), out)
+               for im, out in checks.values())
+    be.close()
+    offered = sum(r.pixels for r in reqs) / duration / 1e9
+    st.update({"duration_s": duration, "rate_hz": 200.0, "offered_gpx_s": offered,
+               "budget_gb": 40, "verified_requests": len(checks), "identical_to_alone": bool(same),
+               "latency": "arrival to device-side completion of the request's batch"})
+    return st
 
 
 if __name__ == "__main__":
