@@ -88,6 +88,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta) batch_kernel_fast(const uns
                                                                       unsigned long long *counter, int *status,
                                                                       const __grid_constant__ KParams kp8,
                                                                       const __grid_constant__ KParams kp16) {
+  __shared__ StripWords words;
   const BatchHeader *hdr = reinterpret_cast<const BatchHeader *>(table);
   const BatchImage *ims = reinterpret_cast<const BatchImage *>(table + sizeof(BatchHeader));
   const long long total = hdr->total_units;
@@ -105,8 +106,8 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta) batch_kernel_fast(const uns
     const ImageView v = view_of(b);
     const long long local = u - b.unit_begin;
     const int64_t ux = local % b.units_x, uy = local / b.units_x;
-    if (b.elem == 1) fast_unit<uint8_t>(v, kp8, ux, uy, hdr->unit_w, hdr->unit_h, nullptr);
-    else fast_unit<uint16_t>(v, kp16, ux, uy, hdr->unit_w, hdr->unit_h, nullptr);
+    if (b.elem == 1) fast_unit<uint8_t>(v, kp8, ux, uy, hdr->unit_w, hdr->unit_h, warp_words(words));
+    else fast_unit<uint16_t>(v, kp16, ux, uy, hdr->unit_w, hdr->unit_h, warp_words(words));
   }
 }
 
@@ -116,6 +117,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta) batch_kernel_redo(const uns
                                                                       unsigned long long *, int *,
                                                                       const __grid_constant__ KParams kp8,
                                                                       const __grid_constant__ KParams kp16) {
+  __shared__ StripWords words;
   const BatchHeader *hdr = reinterpret_cast<const BatchHeader *>(table);
   const BatchImage *ims = reinterpret_cast<const BatchImage *>(table + sizeof(BatchHeader));
   const long long total = hdr->total_units;
@@ -127,9 +129,10 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta) batch_kernel_redo(const uns
     const long long local = u - b.unit_begin;
     const int64_t ux = local % b.units_x, uy = local / b.units_x;
     if (b.elem == 1) {
-      if (kp8.fbound < 0 || kp8.fbound < 255) fast_unit_redo<uint8_t>(v, kp8, ux, uy, hdr->unit_w, hdr->unit_h, nullptr);
+      if (kp8.fbound < 0 || kp8.fbound < 255)
+        fast_unit_redo<uint8_t>(v, kp8, ux, uy, hdr->unit_w, hdr->unit_h, warp_words(words));
     } else {
-      fast_unit_redo<uint16_t>(v, kp16, ux, uy, hdr->unit_w, hdr->unit_h, nullptr);
+      fast_unit_redo<uint16_t>(v, kp16, ux, uy, hdr->unit_w, hdr->unit_h, warp_words(words));
     }
   }
 }
@@ -184,7 +187,8 @@ fx_status build_graph(fx_plan *p, int i) {
   p->smem = unit_smem(p);
   const void *fn = p->fast ? reinterpret_cast<const void *>(&batch_kernel_fast)
                            : reinterpret_cast<const void *>(&batch_kernel_general);
-  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) != cudaSuccess)
+  if (!p->fast &&  // the streaming kernels use static shared memory only
+      cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) != cudaSuccess)
     return FX_ERR_CUDA;
   cudaGraph_t g;
   if (cudaGraphCreate(&g, 0) != cudaSuccess) return FX_ERR_CUDA;

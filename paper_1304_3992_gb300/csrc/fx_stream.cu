@@ -8,10 +8,13 @@ template <typename T, bool kRedoPass>
 __global__ void __launch_bounds__(32 * kWarpsPerCta) stream_kernel(const __grid_constant__ ImageView v,
                                                                   const __grid_constant__ KParams kp,
                                                                   int64_t units_x, int64_t units, int uh) {
+  __shared__ StripWords words;
   const int64_t unit = static_cast<int64_t>(blockIdx.x) * kWarpsPerCta + (threadIdx.x >> 5);
   if (unit >= units) return;  // whole warps only
-  if constexpr (kRedoPass) fast_unit_redo<T>(v, kp, unit % units_x, unit / units_x, kDefaultUnitW, uh, nullptr);
-  else fast_unit<T>(v, kp, unit % units_x, unit / units_x, kDefaultUnitW, uh, nullptr);
+  if constexpr (kRedoPass)
+    fast_unit_redo<T>(v, kp, unit % units_x, unit / units_x, kDefaultUnitW, uh, warp_words(words));
+  else
+    fast_unit<T>(v, kp, unit % units_x, unit / units_x, kDefaultUnitW, uh, warp_words(words));
 }
 
 template <typename T>

@@ -574,31 +574,36 @@ __device__ __forceinline__ uint8_t *unit_marker(const ImageView &v, int64_t ux, 
   return v.out + (uy * uh) * v.out_pitch + ux * st::kOutCols;
 }
 
+// Per-warp shared words of the streaming path (the caller's kernel owns one
+// array of this type per CTA and passes the warp's slice).
+constexpr int kStripWords = 20;
+using StripWords = uint32_t[kWarpsPerCta][kStripWords][32];
+__device__ __forceinline__ uint32_t (*warp_words(StripWords &w))[32] { return w[(threadIdx.x >> 5) % kWarpsPerCta]; }
+
 template <typename T>
 __device__ __forceinline__ void fast_unit(const ImageView &v, const KParams &kp, int64_t ux, int64_t uy, int,
-                                          int uh, unsigned char *) {
+                                          int uh, uint32_t (*words)[32]) {
+  static_assert(st::Strip<T, false>::kWords == kStripWords, "shared word layout");
   if (kp.fbound < 0) return;
-  __shared__ uint32_t words[kWarpsPerCta][st::Strip<T, false>::kWords][32];
   const int64_t X0 = ux * st::kOutCols;
   const int64_t Y0 = v.y_begin + uy * uh;
   const int64_t Y1 = Y0 + uh < v.y_end ? Y0 + uh : v.y_end;
-  st::Strip<T, false> s(v, kp, X0, Y0, Y1, words[(threadIdx.x >> 5) % kWarpsPerCta]);
+  st::Strip<T, false> s(v, kp, X0, Y0, Y1, words);
   if (!s.run() && (threadIdx.x & 31) == 0) *unit_marker(v, ux, uy, uh) = kRedo;
 }
 
 template <typename T>
 __device__ __forceinline__ void fast_unit_redo(const ImageView &v, const KParams &kp, int64_t ux, int64_t uy,
-                                               int, int uh, unsigned char *) {
+                                               int, int uh, uint32_t (*words)[32]) {
   if (kp.fbound >= 0) {
     uint8_t mark = 0;
     if ((threadIdx.x & 31) == 0) mark = *unit_marker(v, ux, uy, uh);
     if (__shfl_sync(st::kFull, mark, 0) != kRedo) return;
   }
-  __shared__ uint32_t words[kWarpsPerCta][st::Strip<T, true>::kWords][32];
   const int64_t X0 = ux * st::kOutCols;
   const int64_t Y0 = v.y_begin + uy * uh;
   const int64_t Y1 = Y0 + uh < v.y_end ? Y0 + uh : v.y_end;
-  st::Strip<T, true> s(v, kp, X0, Y0, Y1, words[(threadIdx.x >> 5) % kWarpsPerCta]);
+  st::Strip<T, true> s(v, kp, X0, Y0, Y1, words);
   s.run();
 }
 
