@@ -190,6 +190,22 @@ fx_status fx_extract_host(fx_plan *plan, const void *img_host, int64_t width, in
                           int64_t out_pitch);
 
 /*
+ * The hybrid median filter of Sec. 3.4 on its own, applied to a uint8/uint16
+ * image (grayscale values rather than the binary extraction map): each output
+ * pixel is the median of (median of the '+' subgroup, median of the 'x'
+ * subgroup, centre), the subgroups being the centre row and column segment
+ * and the two diagonals of the window x window neighbourhood; pixels outside
+ * the image take the nearest image value.
+ *   img, out     device pointers, same dtype; must not overlap
+ *   pitch_bytes  input row pitch; out_pitch_bytes output row pitch (0 = packed)
+ *   window       3 or 5
+ * Errors: FX_ERR_INVALID_ARG, FX_ERR_CUDA.  Allocates nothing.
+ */
+fx_status fx_hybrid_median(const void *img, int64_t width, int64_t height, int64_t pitch_bytes,
+                           fx_dtype dtype, int32_t window, void *out, int64_t out_pitch_bytes,
+                           void *stream);
+
+/*
  * Batched extraction for callers that cannot allocate device memory.  The
  * paper has no counterpart; this entry point exists for deployment.  It does
  * what fx_extract_batch does (same masks, byte for byte) without a plan: its

@@ -77,6 +77,9 @@ _SIGNATURES = {
                                        ctypes.c_int64, ctypes.c_int, ctypes.c_void_p, ctypes.c_int64]),
     "fx_extract_batch_noalloc": (ctypes.c_int, [ctypes.POINTER(Params), ctypes.POINTER(ImageDesc),
                                                 ctypes.c_int32, ctypes.c_void_p]),
+    "fx_hybrid_median": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
+                                        ctypes.c_int, ctypes.c_int32, ctypes.c_void_p, ctypes.c_int64,
+                                        ctypes.c_void_p]),
     "fx_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "fx_version": (ctypes.c_char_p, []),
 }
@@ -174,6 +177,23 @@ def extract(img, params: Params | None = None, out=None, stream=None):
     code = load().fx_extract(img.data_ptr(), w, h, img.stride(0) * img.element_size(), _dtype_code(img),
                              ctypes.byref(p), out.data_ptr(), _stream_ptr(stream))
     _check(code, "fx_extract")
+    return out
+
+
+def hybrid_median(img, window: int = 5, out=None, stream=None):
+    """Grayscale hybrid median (Sec. 3.4) of a 2-D uint8/uint16 CUDA tensor."""
+    import torch
+    if img.dim() != 2 or img.stride(1) != 1:
+        raise ValueError("img must be a 2-D tensor with contiguous rows")
+    h, w = img.shape
+    if out is None:
+        out = torch.empty((h, w), dtype=img.dtype, device=img.device)
+    if out.dtype != img.dtype or tuple(out.shape) != (h, w) or out.stride(1) != 1:
+        raise ValueError("out must match img")
+    code = load().fx_hybrid_median(img.data_ptr(), w, h, img.stride(0) * img.element_size(), _dtype_code(img),
+                                   int(window), out.data_ptr(), out.stride(0) * out.element_size(),
+                                   _stream_ptr(stream))
+    _check(code, "fx_hybrid_median")
     return out
 
 

@@ -1,0 +1,42 @@
+"""The standalone hybrid median filter (Sec. 3.4) on uint8/uint16 values against
+the oracle's grayscale hybrid median (itself pinned to numpy medians): every
+output value must be equal."""
+import numpy as np
+import pytest
+
+import oracle
+from gen import scenes
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.mark.parametrize("window", [3, 5])
+@pytest.mark.parametrize("shape,bits", [((1, 1), 8), ((1, 70), 16), ((53, 1), 8), ((5, 4), 16),
+                                        ((97, 130), 8), ((300, 211), 12), ((67, 1000), 16)])
+def test_hmf_matches_oracle(cuda_lib, window, shape, bits):
+    h, w = shape
+    rng = np.random.default_rng(h * 31 + w + window)
+    if bits == 16:
+        img = rng.integers(0, 65536, size=shape).astype(np.uint16)
+    else:
+        big = scenes.scene(max(w, 8) + 4, max(h, 8) + 4, seed=h + w, n_rects=5, noise_sigma=4.0 * (1 << (bits - 8)),
+                           impulse_frac=0.05, bits=bits)
+        img = np.ascontiguousarray(big[:h, :w])
+    got = cuda_lib.hybrid_median(torch.from_numpy(img).cuda(), window).cpu().numpy()
+    assert np.array_equal(got, oracle.hybrid_median(img, window))
+
+
+def test_hmf_pitched_and_errors(cuda_lib):
+    import ctypes
+    img = scenes.scene(150, 90, seed=3, n_rects=8, noise_sigma=24, impulse_frac=0.02, bits=12)
+    buf = torch.zeros((90, 256), dtype=torch.uint16, device="cuda")
+    buf[:, :150] = torch.from_numpy(img).cuda()
+    obuf = torch.full((90, 200), 7, dtype=torch.uint16, device="cuda")
+    cuda_lib.hybrid_median(buf[:, :150], 5, out=obuf[:, :150])
+    assert np.array_equal(obuf[:, :150].cpu().numpy(), oracle.hybrid_median(img, 5))
+    assert (obuf[:, 150:].cpu().numpy() == 7).all()
+    lib = cuda_lib.load()
+    t = torch.zeros((8, 8), dtype=torch.uint16, device="cuda")
+    assert lib.fx_hybrid_median(t.data_ptr(), 8, 8, 16, 2, 4, obuf.data_ptr(), 0, None) == 1
+    assert lib.fx_hybrid_median(t.data_ptr(), 8, 8, 16, 2, 5, t.data_ptr(), 0, None) == 1
