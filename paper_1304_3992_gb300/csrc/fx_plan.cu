@@ -84,7 +84,7 @@ __global__ void __launch_bounds__(256) batch_kernel_general(const unsigned char 
   }
 }
 
-__global__ void __launch_bounds__(32 * kWarpsPerCta) batch_kernel_fast(const unsigned char *table,
+__global__ void __launch_bounds__(32 * kWarpsPerCta, 3) batch_kernel_fast(const unsigned char *table,
                                                                       unsigned long long *counter, int *status,
                                                                       const __grid_constant__ KParams kp8,
                                                                       const __grid_constant__ KParams kp16) {
@@ -113,7 +113,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta) batch_kernel_fast(const uns
 
 // Second pass of the streaming path: every warp walks the units with a static
 // stride and recomputes, on the integer path, the strips the first pass marked.
-__global__ void __launch_bounds__(32 * kWarpsPerCta) batch_kernel_redo(const unsigned char *table,
+__global__ void __launch_bounds__(32 * kWarpsPerCta, 3) batch_kernel_redo(const unsigned char *table,
                                                                       unsigned long long *, int *,
                                                                       const __grid_constant__ KParams kp8,
                                                                       const __grid_constant__ KParams kp16) {

@@ -5,7 +5,7 @@ namespace fx {
 namespace {
 
 template <typename T, bool kRedoPass>
-__global__ void __launch_bounds__(32 * kWarpsPerCta) stream_kernel(const __grid_constant__ ImageView v,
+__global__ void __launch_bounds__(32 * kWarpsPerCta, 3) stream_kernel(const __grid_constant__ ImageView v,
                                                                   const __grid_constant__ KParams kp,
                                                                   int64_t units_x, int64_t units, int uh) {
   __shared__ StripWords words;

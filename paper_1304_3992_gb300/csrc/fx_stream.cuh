@@ -1,13 +1,15 @@
 // fx_stream.cuh -- the streaming fast path (device code).
 //
-// One warp computes a strip of 112 output columns over a range of output rows,
-// walking down the image one row per step.  Lane l owns the four adjacent
-// window columns xs + 4l .. xs + 4l + 3 of a 128-column window that starts 8
+// One warp computes a strip of 52 output columns over a range of output rows,
+// walking down the image one row per step.  Lane l owns the two adjacent
+// window columns xs + 2l, xs + 2l + 1 of a 64-column window that starts 6
 // columns left of the strip (the halo the stages need: 2 LoG + 1 crossing +
-// 2 median, rounded up to the 8-column alignment of the loads).
+// 2 median, rounded up to the even column alignment of the loads).  Two
+// columns per lane keep the per-lane state small, so that several warps per
+// scheduler hide each other's latencies.
 //
 // Per step (one input row t; every value stays in registers):
-//   - one coalesced load of the lane's 4 pixels (plus 2 + 2 halo pixels from
+//   - one coalesced load of the lane's 2 pixels (plus 2 + 2 halo pixels from
 //     the neighbouring lanes by shuffle);
 //   - horizontal sums h1 = I(x-1) + I(x+1), h2 = I(x-2) + I(x+2) and the
 //     3- and 5-wide sums of squares (integer);
@@ -18,8 +20,8 @@
 //   - for row c' = t-3 (whose four neighbours are now known): the sign of L,
 //     the sign of -L, the signs of the east and south edge sums L(p)+L(q) and
 //     the contrast test (Sec. 3.2), each packed as one bit per pixel.
-// Bits are packed into 32-bit words covering 8 rows x the lane's 4 columns
-// (bit 28 - 4r + j for row r, column j).  Every 8 rows the zero-crossing rule
+// Bits are packed into 32-bit words covering 16 rows x the lane's 2 columns
+// (bit 30 - 2r + j for row r, column j).  Every 16 rows the zero-crossing rule
 // (reading R3), the extraction, the OR of the two maps (Sec. 4.1) and the
 // hybrid median (Sec. 3.4, reading R6) run as bitwise logic on those words,
 // and the finished mask rows are stored.
@@ -37,34 +39,33 @@
 
 namespace fx {
 
-constexpr int kDefaultUnitW = 112;
+constexpr int kDefaultUnitW = 52;
 constexpr int kDefaultUnitH = 512;
 constexpr int kNumUnitShapes = 4;
-constexpr int kUnitShapes[kNumUnitShapes][2] = {{112, 256}, {112, 512}, {112, 1024}, {112, 2048}};
+constexpr int kUnitShapes[kNumUnitShapes][2] = {{52, 256}, {52, 512}, {52, 1024}, {52, 2048}};
 constexpr int kMaxCtasPerSm = 8;
 constexpr int kWarpsPerCta = 4;
 
-inline bool fast_unit_shape_ok(int w, int h) { return w == 112 && h >= 8 && h <= 8192 && h % 8 == 0; }
+inline bool fast_unit_shape_ok(int w, int h) { return w == 52 && h >= 16 && h <= 8192 && h % 16 == 0; }
 inline size_t fast_smem_bytes(int, int, int) { return 0; }
 
 namespace st {
 
 constexpr unsigned kFull = 0xffffffffu;
-constexpr int kLeftHalo = 8;
-constexpr int kOutCols = 112;
-constexpr uint32_t MJ0 = 0x11111111u, MJ3 = 0x88888888u, MJ01 = 0x33333333u, MJ23 = 0xCCCCCCCCu;
+constexpr int kLeftHalo = 6;
+constexpr int kOutCols = 52;
+constexpr int kWinCols = 64;
+constexpr uint32_t M0 = 0x55555555u, M1 = 0xAAAAAAAAu;  // bits of column 0 / column 1
 
 // Neighbour words: bit of pixel p in the result = bit of its neighbour.
 // own = this lane's word, nx / pv = the next / previous lane's word of the same
-// rows, nb / pb = this lane's word of the next / previous 8 rows.
-__device__ __forceinline__ uint32_t e1(uint32_t o, uint32_t nx) { return ((o >> 1) & ~MJ3) | ((nx << 3) & MJ3); }
-__device__ __forceinline__ uint32_t w1(uint32_t o, uint32_t pv) { return ((o << 1) & ~MJ0) | ((pv >> 3) & MJ0); }
-__device__ __forceinline__ uint32_t e2(uint32_t o, uint32_t nx) { return ((o >> 2) & MJ01) | ((nx << 2) & MJ23); }
-__device__ __forceinline__ uint32_t w2(uint32_t o, uint32_t pv) { return ((o << 2) & MJ23) | ((pv >> 2) & MJ01); }
-__device__ __forceinline__ uint32_t n1(uint32_t o, uint32_t pb) { return (o >> 4) | (pb << 28); }
-__device__ __forceinline__ uint32_t s1(uint32_t o, uint32_t nb) { return (o << 4) | (nb >> 28); }
-__device__ __forceinline__ uint32_t n2(uint32_t o, uint32_t pb) { return (o >> 8) | (pb << 24); }
-__device__ __forceinline__ uint32_t s2(uint32_t o, uint32_t nb) { return (o << 8) | (nb >> 24); }
+// rows, nb / pb = this lane's word of the next / previous 16 rows.
+__device__ __forceinline__ uint32_t e1(uint32_t o, uint32_t nx) { return ((o >> 1) & M0) | ((nx << 1) & M1); }
+__device__ __forceinline__ uint32_t w1(uint32_t o, uint32_t pv) { return ((o << 1) & M1) | ((pv >> 1) & M0); }
+__device__ __forceinline__ uint32_t n1(uint32_t o, uint32_t pb) { return __funnelshift_r(o, pb, 2); }
+__device__ __forceinline__ uint32_t s1(uint32_t o, uint32_t nb) { return __funnelshift_l(nb, o, 2); }
+__device__ __forceinline__ uint32_t n2(uint32_t o, uint32_t pb) { return __funnelshift_r(o, pb, 4); }
+__device__ __forceinline__ uint32_t s2(uint32_t o, uint32_t nb) { return __funnelshift_l(nb, o, 4); }
 
 __device__ __forceinline__ void fadd(uint32_t a, uint32_t b, uint32_t c, uint32_t &s, uint32_t &k) {
   s = a ^ b ^ c;
@@ -168,24 +169,30 @@ struct Strip {
   int lane;
   bool check, border, vload, vstore;
   int bl_lane, bl_slot, br_lane, br_slot;
-  uint32_t outmask_l, outmask_r;  // this lane's slots left of / right of the image (MJ0 << j)
+  uint32_t outmask_l, outmask_r;  // this lane's slots left of / right of the image (M0 << j)
 
   // Rings of period 4 (slot of row t = t & 3).  The row four steps back is
   // read before the newest row overwrites its slot.
-  V f_[4][4], h1_[4][4], h2_[4][4];
-  Q c3_[4][4], c5_[4][4];
-  V L_[2][4][4];
+  V f_[4][2], h1_[4][2], h2_[4][2];
+  Q c3_[4][2], c5_[4][2];
+  V L_[2][4][2];
   V LW_[2][4], LE_[2][4];
-  uint32_t S_[2][4][4];
-  uint32_t raw_[4][2];
+  uint32_t S_[2][4][2];
+  uint32_t raw_[4];
   uint32_t vmax_;
   uint32_t acc_[12];
-  // Words of earlier blocks, touched once per 8 rows, live in shared memory:
-  // kBlk.. = previous block (12 words), kPrev.. = neg / pos / sS of the block
-  // before it (6), kMA / kMB = mask words of the two previous blocks.
+  // Words of earlier blocks, touched once per 16 rows, live in shared memory:
+  // kBlk.. = previous block (12 words), kPneg / kPpos / kPsS = neg / pos / sS of
+  // the block before it, kMA / kMB = mask words of the two previous blocks.
   uint32_t (*sw_)[32];
   static constexpr int kBlk = 0, kPneg = 12, kPpos = 14, kPsS = 16, kMA = 18, kMB = 19, kWords = 20;
   __device__ __forceinline__ uint32_t &blk(int i) { return sw_[kBlk + i][lane]; }
+
+  // load state: rows relative to Y0
+  int32_t rlo, rhi, Hrel, Y0rel;
+  const unsigned char *rowY0;
+  bool cload;      // this lane's 2 columns are inside the image and aligned
+  int32_t xcl[2];  // clamped columns (only when !cload)
 
   __device__ Strip(const ImageView &v_, const KParams &kp_, int64_t x0, int64_t y0, int64_t y1,
                    uint32_t (*words)[32])
@@ -195,95 +202,78 @@ struct Strip {
     H = v.height;
     xs = X0 - kLeftHalo;
     check = !kInt && kp.fbound < (sizeof(T) == 1 ? 255 : 65535);
-    border = xs < 0 || xs + 128 > W;
+    border = xs < 0 || xs + kWinCols > W;
     const uintptr_t base = reinterpret_cast<uintptr_t>(v.img);
-    vload = (base % (4 * sizeof(T)) == 0) && (v.pitch % (4 * sizeof(T)) == 0) && (xs % 4 == 0);
-    {
-      const int64_t lo = v.row0 > 0 ? v.row0 : 0, hi = (v.row_lim < H ? v.row_lim : H) - 1;
-      rlo = static_cast<int32_t>(lo - Y0);
-      Hrel = static_cast<int32_t>(H - Y0);
-      Y0rel = static_cast<int32_t>(Y0 < (1 << 30) ? Y0 : (1 << 30));
-      rhi = static_cast<int32_t>(hi - Y0);
-      const int64_t x = xs + 4 * lane;
-      cload = vload && x >= 0 && x + 3 < W;
-      for (int j = 0; j < 4; ++j) xcl[j] = static_cast<int32_t>(x + j < 0 ? 0 : (x + j >= W ? W - 1 : x + j));
-      rowY0 = static_cast<const unsigned char *>(v.img) + (Y0 - v.row0) * v.pitch +
-              (cload ? x * static_cast<int64_t>(sizeof(T)) : 0);
-    }
-    vstore = (reinterpret_cast<uintptr_t>(v.out) % 4 == 0) && (v.out_pitch % 4 == 0) && (xs % 4 == 0);
+    vload = (base % (2 * sizeof(T)) == 0) && (v.pitch % (2 * sizeof(T)) == 0) && (xs % 2 == 0);
+    vstore = (reinterpret_cast<uintptr_t>(v.out) % 2 == 0) && (v.out_pitch % 2 == 0) && (xs % 2 == 0);
     const int64_t bl = -xs, br = W - 1 - xs;  // window columns of image columns 0 and W-1
-    bl_lane = bl > 0 ? static_cast<int>(bl >> 2) : 0;
-    bl_slot = bl > 0 ? static_cast<int>(bl & 3) : 0;
-    br_lane = br < 127 ? static_cast<int>((br < 0 ? 0 : br) >> 2) : 31;
-    br_slot = br < 127 ? static_cast<int>((br < 0 ? 0 : br) & 3) : 3;
+    bl_lane = bl > 0 ? static_cast<int>(bl >> 1) : 0;
+    bl_slot = bl > 0 ? static_cast<int>(bl & 1) : 0;
+    br_lane = br < kWinCols - 1 ? static_cast<int>((br < 0 ? 0 : br) >> 1) : 31;
+    br_slot = br < kWinCols - 1 ? static_cast<int>((br < 0 ? 0 : br) & 1) : 1;
     outmask_l = outmask_r = 0;
-    for (int j = 0; j < 4; ++j) {
-      const int64_t xg = xs + 4 * lane + j;
-      if (xg < 0) outmask_l |= MJ0 << j;
-      if (xg >= W) outmask_r |= MJ0 << j;
+    const int64_t x = xs + 2 * lane;
+    for (int j = 0; j < 2; ++j) {
+      if (x + j < 0) outmask_l |= M0 << j;
+      if (x + j >= W) outmask_r |= M0 << j;
     }
+    const int64_t lo = v.row0 > 0 ? v.row0 : 0, hi = (v.row_lim < H ? v.row_lim : H) - 1;
+    rlo = static_cast<int32_t>(lo - Y0);
+    rhi = static_cast<int32_t>(hi - Y0);
+    Hrel = static_cast<int32_t>(H - Y0);
+    Y0rel = static_cast<int32_t>(Y0 < (1 << 30) ? Y0 : (1 << 30));
+    cload = vload && x >= 0 && x + 1 < W;
+    for (int j = 0; j < 2; ++j) xcl[j] = static_cast<int32_t>(x + j < 0 ? 0 : (x + j >= W ? W - 1 : x + j));
+    rowY0 = static_cast<const unsigned char *>(v.img) + (Y0 - v.row0) * v.pitch +
+            (cload ? x * static_cast<int64_t>(sizeof(T)) : 0);
     vmax_ = 0;
     for (int i = 0; i < 12; ++i) acc_[i] = 0;
     for (int i = 0; i < kWords; ++i) sw_[i][lane] = 0;
 #pragma unroll
     for (int s = 0; s < 4; ++s) {
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
+      for (int j = 0; j < 2; ++j) {
         f_[s][j] = h1_[s][j] = h2_[s][j] = V(0);
         c3_[s][j] = c5_[s][j] = Q(0);
         L_[0][s][j] = L_[1][s][j] = V(0);
         S_[0][s][j] = S_[1][s][j] = 0;
       }
       LW_[0][s] = LW_[1][s] = LE_[0][s] = LE_[1][s] = V(0);
+      raw_[s] = 0;
     }
   }
 
-  // Row t of the image (clamped) into raw slot S, as two words of 16-bit pairs.
-  // Row t of the image (clamped) into raw slot S, as two words of 16-bit pairs.
+  // Row t (relative to Y0) into raw slot S as a 16-bit pair (column 0 low).
   // Rows outside the image clamp to it (reading R2); rows outside the buffer
   // (a row band) clamp to the buffer: they feed only rows that are not stored.
-  // rlo / rhi: first / last loadable row relative to Y0; colp: this lane's
-  // first column in row Y0 (or, with cload, the row base).
-  int32_t rlo, rhi;
-  int32_t Hrel, Y0rel;  // H - Y0 and Y0 (clamped to int32 range)
-  const unsigned char *rowY0;
-  bool cload;  // this lane's 4 columns are inside the image and aligned
-  int32_t xcl[4];  // clamped columns (only when !cload)
-
   template <int S>
-  __device__ __forceinline__ void load_row(int32_t tr) {  // tr = t - Y0
+  __device__ __forceinline__ void load_row(int32_t tr) {
     const int32_t yr = tr < rlo ? rlo : (tr > rhi ? rhi : tr);
     const unsigned char *row = rowY0 + static_cast<int64_t>(yr) * v.pitch;
     if (cload) {
       if constexpr (sizeof(T) == 2) {
-        const uint2 q = __ldg(reinterpret_cast<const uint2 *>(row));
-        raw_[S][0] = q.x;
-        raw_[S][1] = q.y;
+        raw_[S] = __ldg(reinterpret_cast<const uint32_t *>(row));
       } else {
-        const uint32_t q = __ldg(reinterpret_cast<const uint32_t *>(row));
-        raw_[S][0] = __byte_perm(q, 0, 0x4140);
-        raw_[S][1] = __byte_perm(q, 0, 0x4342);
+        raw_[S] = __byte_perm(static_cast<uint32_t>(__ldg(reinterpret_cast<const uint16_t *>(row))), 0, 0x4140);
       }
     } else {
-      uint32_t u[4];
-#pragma unroll
-      for (int j = 0; j < 4; ++j) u[j] = static_cast<uint32_t>(__ldg(reinterpret_cast<const T *>(row) + xcl[j]));
-      raw_[S][0] = u[0] | (u[1] << 16);
-      raw_[S][1] = u[2] | (u[3] << 16);
+      const uint32_t u0 = static_cast<uint32_t>(__ldg(reinterpret_cast<const T *>(row) + xcl[0]));
+      const uint32_t u1 = static_cast<uint32_t>(__ldg(reinterpret_cast<const T *>(row) + xcl[1]));
+      raw_[S] = u0 | (u1 << 16);
     }
   }
 
   // Replace the values of window columns outside the image by the value of the
   // nearest image column (reading R2 for a stage array).
-  __device__ __forceinline__ void fix_cols(V x[4]) {
-    const V sl = bl_slot == 0 ? x[0] : bl_slot == 1 ? x[1] : bl_slot == 2 ? x[2] : x[3];
-    const V sr = br_slot == 0 ? x[0] : br_slot == 1 ? x[1] : br_slot == 2 ? x[2] : x[3];
+  __device__ __forceinline__ void fix_cols(V x[2]) {
+    const V sl = bl_slot == 0 ? x[0] : x[1];
+    const V sr = br_slot == 0 ? x[0] : x[1];
     const V lv = __shfl_sync(kFull, sl, bl_lane);
     const V rv = __shfl_sync(kFull, sr, br_lane);
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      if (outmask_l & (MJ0 << j)) x[j] = lv;
-      if (outmask_r & (MJ0 << j)) x[j] = rv;
+    for (int j = 0; j < 2; ++j) {
+      if (outmask_l & (M0 << j)) x[j] = lv;
+      if (outmask_r & (M0 << j)) x[j] = rv;
     }
   }
 
@@ -291,59 +281,58 @@ struct Strip {
   __device__ __forceinline__ uint32_t fix_cols_bits(uint32_t m) {
     const uint32_t ml = __shfl_sync(kFull, m, bl_lane);
     const uint32_t mr = __shfl_sync(kFull, m, br_lane);
-    const uint32_t repl = ((ml >> bl_slot) & MJ0) * 0xFu;
-    const uint32_t repr = ((mr >> br_slot) & MJ0) * 0xFu;
+    const uint32_t repl = ((ml >> bl_slot) & M0) * 0x3u;
+    const uint32_t repr = ((mr >> br_slot) & M0) * 0x3u;
     m = (m & ~outmask_l) | (repl & outmask_l);
     m = (m & ~outmask_r) | (repr & outmask_r);
     return m;
   }
 
-  template <int S, bool kL, bool kPack>
+  template <int S>
   __device__ __forceinline__ void step(int32_t t) {  // t relative to Y0, S = t & 3
     load_row<(S + 2) & 3>(t + 2);
-    const uint32_t w0 = raw_[S][0], w1v = raw_[S][1];
-    if (check) vmax_ = __vmaxu2(vmax_, __vmaxu2(w0, w1v));
-    const uint32_t hl = __shfl_up_sync(kFull, w1v, 1);
-    const uint32_t hr = __shfl_down_sync(kFull, w0, 1);
-    const uint32_t u[8] = {hl & 0xFFFFu, hl >> 16, w0 & 0xFFFFu, w0 >> 16,
-                           w1v & 0xFFFFu, w1v >> 16, hr & 0xFFFFu, hr >> 16};
-    V fv[8];
-    Q sq[8];
+    const uint32_t w = raw_[S];
+    if (check) vmax_ = __vmaxu2(vmax_, w);
+    const uint32_t hl = __shfl_up_sync(kFull, w, 1);    // columns -2, -1
+    const uint32_t hr = __shfl_down_sync(kFull, w, 1);  // columns 2, 3
+    const uint32_t u[6] = {hl & 0xFFFFu, hl >> 16, w & 0xFFFFu, w >> 16, hr & 0xFFFFu, hr >> 16};
+    V fv[6];
+    Q sq[6];
 #pragma unroll
-    for (int k = 0; k < 8; ++k) {
+    for (int k = 0; k < 6; ++k) {
       fv[k] = A::cvt(u[k]);
       sq[k] = A::sq(u[k]);
     }
-    V fn[4], h1n[4], h2n[4];
-    Q c3n[4], c5n[4];
+    V fn[2], h1n[2], h2n[2];
+    Q c3n[2], c5n[2];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
+    for (int j = 0; j < 2; ++j) {
       fn[j] = fv[j + 2];
       h1n[j] = fv[j + 1] + fv[j + 3];
       h2n[j] = fv[j] + fv[j + 4];
       c3n[j] = sq[j + 1] + sq[j + 2] + sq[j + 3];
       c5n[j] = c3n[j] + sq[j] + sq[j + 4];
     }
-    if constexpr (kL) centre<S>(t - 2, fn, h1n, h2n, c5n);
+    centre<S>(t - 2, fn, h1n, h2n, c5n);
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
+    for (int j = 0; j < 2; ++j) {
       f_[S][j] = fn[j];
       h1_[S][j] = h1n[j];
       h2_[S][j] = h2n[j];
       c3_[S][j] = c3n[j];
       c5_[S][j] = c5n[j];
     }
-    if constexpr (kPack) pack<S>();
+    pack<S>();
   }
 
   // LoG responses and the standard-deviation test for the centre row c = t - 2
   // (row t arrives in fn / h1n / h2n / c5n; slot S still holds row t - 4).
   template <int S>
-  __device__ __forceinline__ void centre(int32_t c, const V fn[4], const V h1n[4], const V h2n[4],
-                                         const Q c5n[4]) {
+  __device__ __forceinline__ void centre(int32_t c, const V fn[2], const V h1n[2], const V h2n[2],
+                                         const Q c5n[2]) {
     constexpr int c0 = (S + 2) & 3, m1 = (S + 1) & 3, p1 = (S + 3) & 3, m2 = S;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
+    for (int j = 0; j < 2; ++j) {
       const V R0 = f_[c0][j];
       const V R1 = h1_[c0][j] + (f_[m1][j] + f_[p1][j]);
       const V R2 = h1_[m1][j] + h1_[p1][j];
@@ -372,7 +361,7 @@ struct Strip {
 #pragma unroll
       for (int f = 0; f < 2; ++f)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) L_[f][c0][j] = L_[f][m1][j];
+        for (int j = 0; j < 2; ++j) L_[f][c0][j] = L_[f][m1][j];
     }
     if (border) {
       fix_cols(L_[0][c0]);
@@ -382,11 +371,11 @@ struct Strip {
 #pragma unroll
       for (int f = 0; f < 2; ++f)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) L_[f][m1][j] = L_[f][c0][j];
+        for (int j = 0; j < 2; ++j) L_[f][m1][j] = L_[f][c0][j];
     }
 #pragma unroll
     for (int f = 0; f < 2; ++f) {
-      LW_[f][c0] = __shfl_up_sync(kFull, L_[f][c0][3], 1);
+      LW_[f][c0] = __shfl_up_sync(kFull, L_[f][c0][1], 1);
       LE_[f][c0] = __shfl_down_sync(kFull, L_[f][c0][0], 1);
     }
   }
@@ -398,11 +387,11 @@ struct Strip {
 #pragma unroll
     for (int f = 0; f < 2; ++f) {
 #pragma unroll
-      for (int jj = 0; jj < 4; ++jj) {
-        const int j = 3 - jj;
+      for (int jj = 0; jj < 2; ++jj) {
+        const int j = 1 - jj;
         const V Lc = L_[f][r][j], Ln = L_[f][rn][j], Ls = L_[f][rs][j];
-        const V Lw = j > 0 ? L_[f][r][j > 0 ? j - 1 : 0] : LW_[f][r];
-        const V Le = j < 3 ? L_[f][r][j < 3 ? j + 1 : 3] : LE_[f][r];
+        const V Lw = j > 0 ? L_[f][r][0] : LW_[f][r];
+        const V Le = j < 1 ? L_[f][r][1] : LE_[f][r];
         put(acc_[5 * f + 0], A::bits(Lc));
         put(acc_[5 * f + 1], A::bits(A::neg(Lc)));
         put(acc_[5 * f + 2], A::bits(Lc + Le));
@@ -412,15 +401,15 @@ struct Strip {
         put(acc_[5 * f + 4], A::cfail(kp, f, mx, mn));
       }
     }
-#pragma unroll
-    for (int jj = 0; jj < 4; ++jj) put(acc_[10], S_[0][r][3 - jj]);
+    put(acc_[10], S_[0][r][1]);
+    put(acc_[10], S_[0][r][0]);
     if (!kp.sd_same) {
-#pragma unroll
-      for (int jj = 0; jj < 4; ++jj) put(acc_[11], S_[1][r][3 - jj]);
+      put(acc_[11], S_[1][r][1]);
+      put(acc_[11], S_[1][r][0]);
     }
   }
 
-  // Block b = g - 1 (words blk_): zero crossings, extraction, OR (the mask M).
+  // Block b = g - 1 (words blk): zero crossings, extraction, OR (the mask M).
   __device__ __forceinline__ uint32_t mask_block(int64_t b) {
     uint32_t m = 0;
 #pragma unroll
@@ -446,19 +435,19 @@ struct Strip {
       m |= (znz | z0) & ~cf & sd;
     }
     // replicated borders for the mask (reading R2)
-    const int64_t r0 = Y0 - 3 + 8 * b;  // image row of bit-row 0
+    const int64_t r0 = Y0 - 3 + 16 * b;  // image row of bit-row 0
     if (r0 < 0) {  // top: rows -3..-1 take row 0 (bit-row 3)
-      const uint32_t nib = (m >> 16) & 0xFu;
-      m = (m & 0x000FFFFFu) | (nib << 20) | (nib << 24) | (nib << 28);
+      const uint32_t pr = (m >> 24) & 0x3u;
+      m = (m & 0x03FFFFFFu) | (pr << 26) | (pr << 28) | (pr << 30);
     }
-    if (r0 + 7 >= H) {  // bottom: rows >= H take row H - 1
+    if (r0 + 15 >= H) {  // bottom: rows >= H take row H - 1
       const int64_t rH = H - 1 - r0;
       if (rH >= 0) {
-        const uint32_t keep = 0xFFFFFFFFu << (4 * (7 - rH));
-        const uint32_t nib = (m >> (28 - 4 * rH)) & 0xFu;
-        m = (m & keep) | ((nib * 0x11111111u) & ~keep);
+        const uint32_t keep = 0xFFFFFFFFu << (2 * (15 - rH));
+        const uint32_t pr = (m >> (30 - 2 * rH)) & 0x3u;
+        m = (m & keep) | ((pr * 0x55555555u) & ~keep);
       } else {
-        m = (sw_[kMA][lane] & 0xFu) * 0x11111111u;
+        m = (sw_[kMA][lane] & 0x3u) * 0x55555555u;
       }
     }
     if (border) m = fix_cols_bits(m);
@@ -476,12 +465,10 @@ struct Strip {
       const uint32_t xP = __shfl_up_sync(kFull, next, 1), xX = __shfl_down_sync(kFull, next, 1);
       const uint32_t E1o = e1(own, oX), W1o = w1(own, oP), E1p = e1(prev, pX), W1p = w1(prev, pP);
       const uint32_t E1n = e1(next, xX), W1n = w1(next, xP);
-      if (k == 5) {
-        const uint32_t E2o = e2(own, oX), W2o = w2(own, oP), E2p = e2(prev, pX), W2p = w2(prev, pP);
-        const uint32_t E2n = e2(next, xX), W2n = w2(next, xP);
-        const uint32_t plus[9] = {own, E1o, W1o, E2o, W2o, n1(own, prev), s1(own, next), n2(own, prev), s2(own, next)};
+      if (k == 5) {  // two columns over: the neighbour lane's word itself
+        const uint32_t plus[9] = {own, E1o, W1o, oX, oP, n1(own, prev), s1(own, next), n2(own, prev), s2(own, next)};
         const uint32_t cross[9] = {own, n1(E1o, E1p), n1(W1o, W1p), s1(E1o, E1n), s1(W1o, W1n),
-                                   n2(E2o, E2p), n2(W2o, W2p), s2(E2o, E2n), s2(W2o, W2n)};
+                                   n2(oX, pX), n2(oP, pP), s2(oX, xX), s2(oP, xP)};
         h = maj3(maj9(plus), maj9(cross), own);
       } else {
         const uint32_t plus[5] = {own, E1o, W1o, n1(own, prev), s1(own, next)};
@@ -489,28 +476,28 @@ struct Strip {
         h = maj3(maj5(plus), maj5(cross), own);
       }
     }
-    const int64_t x = xs + 4 * lane;
-    const bool lane_out = lane >= 2 && lane < 30 && x < W;
+    const int64_t x = xs + 2 * lane;
+    const bool lane_out = lane >= 3 && lane < 29 && x < W;
     if (!lane_out) return;
-    const bool full = vstore && x + 3 < W;
+    const bool full = vstore && x + 1 < W;
+    const int64_t ybase = Y0 - 3 + 16 * b;
+    uint8_t *dst = v.out + (ybase - v.y_begin) * v.out_pitch + x;
 #pragma unroll
-    for (int r = 0; r < 8; ++r) {
-      const int64_t y = Y0 - 3 + 8 * b + r;
+    for (int r = 0; r < 16; ++r, dst += v.out_pitch) {
+      const int64_t y = ybase + r;
       if (y < Y0 || y >= Y1) continue;
-      const uint32_t nib = (h >> (28 - 4 * r)) & 0xFu;
-      const uint32_t bytes = (nib * 0x00204081u) & 0x01010101u;
-      uint8_t *dst = v.out + (y - v.y_begin) * v.out_pitch + x;
+      const uint32_t pr = (h >> (30 - 2 * r)) & 0x3u;
+      const uint32_t bytes = (pr | (pr << 7)) & 0x0101u;
       if (full) {
-        *reinterpret_cast<uint32_t *>(dst) = bytes;
+        *reinterpret_cast<uint16_t *>(dst) = static_cast<uint16_t>(bytes);
       } else {
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-          if (x + j < W) dst[j] = static_cast<uint8_t>((bytes >> (8 * j)) & 1u);
+        dst[0] = static_cast<uint8_t>(bytes & 1u);
+        if (x + 1 < W) dst[1] = static_cast<uint8_t>(bytes >> 8);
       }
     }
   }
 
-  // End of the 8 steps of group g: block g is packed in acc_.
+  // End of the 16 steps of group g: block g is packed in acc_.
   __device__ __forceinline__ bool end_group(int64_t g) {
     if (check) {
       const uint32_t m = max(vmax_ & 0xFFFFu, vmax_ >> 16);
@@ -533,24 +520,24 @@ struct Strip {
   }
 
   __device__ __forceinline__ void four_steps(int32_t t0) {  // t0 = 4k relative to Y0
-    step<0, true, true>(t0);
-    step<1, true, true>(t0 + 1);
-    step<2, true, true>(t0 + 2);
-    step<3, true, true>(t0 + 3);
+    step<0>(t0);
+    step<1>(t0 + 1);
+    step<2>(t0 + 2);
+    step<3>(t0 + 3);
   }
 
   __device__ bool run() {
     // Rows Y0-8 .. Y0-1 (k = -2, -1) fill the rings; they compute responses and
-    // bits of rows no output depends on.  Bit blocks span 8 rows (two
-    // iterations); block b covers rows [Y0 - 3 + 8b, Y0 + 5 + 8b) and its
-    // median is stored at the end of block b + 2.
+    // bits of rows no output depends on.  Bit blocks span 16 rows (four
+    // iterations); block b covers rows [Y0 - 3 + 16b, Y0 + 13 + 16b) and its
+    // median is stored at the end of group b + 2.
     load_row<0>(-8);
     load_row<1>(-7);
-    const int32_t bmax = static_cast<int32_t>((Y1 - Y0 + 2) / 8);
-    const int32_t iters = 2 * (bmax + 3);
+    const int32_t bmax = static_cast<int32_t>((Y1 - Y0 + 2) / 16);
+    const int32_t iters = 4 * (bmax + 3);
     for (int32_t k = -2; k < iters; ++k) {
       four_steps(4 * k);
-      if ((k & 1) && !end_group(k >> 1)) return false;
+      if ((k & 3) == 3 && !end_group(k >> 2)) return false;
     }
     return true;
   }
@@ -558,7 +545,7 @@ struct Strip {
 
 }  // namespace st
 
-// Work units: output columns [112 ux, 112 ux + 112), rows [y_begin + uh uy,
+// Work units: output columns [52 ux, 52 ux + 52), rows [y_begin + uh uy,
 // + uh) of the view, computed by the calling warp.
 //
 // fast_unit runs the FP32 path.  A strip that meets a value above
