@@ -290,8 +290,8 @@ struct Strip {
 
   template <int S>
   __device__ __forceinline__ void step(int32_t t) {  // t relative to Y0, S = t & 3
-    load_row<(S + 2) & 3>(t + 2);
     const uint32_t w = raw_[S];
+    load_row<S>(t + 4);  // four rows ahead, into the slot just read
     if (check) vmax_ = __vmaxu2(vmax_, w);
     const uint32_t hl = __shfl_up_sync(kFull, w, 1);    // columns -2, -1
     const uint32_t hr = __shfl_down_sync(kFull, w, 1);  // columns 2, 3
@@ -533,6 +533,8 @@ struct Strip {
     // median is stored at the end of group b + 2.
     load_row<0>(-8);
     load_row<1>(-7);
+    load_row<2>(-6);
+    load_row<3>(-5);
     const int32_t bmax = static_cast<int32_t>((Y1 - Y0 + 2) / 16);
     const int32_t iters = 4 * (bmax + 3);
     for (int32_t k = -2; k < iters; ++k) {
