@@ -46,6 +46,7 @@ def parse():
     ap.add_argument("--impl", default="fx", choices=["fx", "reference"])
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-vs-plain comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-fp32", action="store_true", help="skip the FP32-LoG mode measurement")
     ap.add_argument("--side", type=int, default=SIDE, help="band side (default 16384)")
     ap.add_argument("--serve-duration", type=float, default=10.0,
                     help="seconds of the Poisson serving run (0 skips it; 60 is the full workload)")
@@ -291,6 +292,11 @@ def main():
     elapsed_ms = max_over_ranks(elapsed_ms, dev)
     value = aggregate_gpx_s(px_step, K, elapsed_ms, world)
 
+    # ---- the FP32-LoG mode (non-integer masks) on the same bands
+    fp32 = None
+    if not args.no_fp32:
+        fp32 = bench_fp32_log(fx, torch, stream, bands, outs, max(3, args.warmup), min(K, 10))
+
     # ---- end to end through the C ABI on pinned host buffers
     h_in = [torch.from_numpy(b).pin_memory() for b in bands_np]
     h_out = [torch.empty(b.shape, dtype=torch.uint8).pin_memory() for b in bands_np]
@@ -361,10 +367,41 @@ def main():
             # per band: the streaming kernel and the integer redo check (12-bit data
             # is within the FP32-exact bound, so the redo kernel only reads markers)
             "gpu_launches": K * BANDS * 2, "clocks": clk, "batched": batched, "serving": serving,
+            "fp32_log": fp32,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def bench_fp32_log(fx, torch, stream, bands, outs_int, warmup, steps):
+    """fx_extract in the FP32-LoG mode (non-integer masks, FP32 responses) over
+    the same bands: throughput, mean kernel-pair time per band, and the share of
+    pixels whose mask differs from the integer-mask mode (different masks, so
+    some differ by design)."""
+    p32 = fx.make_params(fx.FX_U16, 12, log_mode=fx.FX_LOG_FP32)
+    outs = [torch.empty_like(o) for o in outs_int]
+    for _ in range(warmup):
+        for b, o in zip(bands, outs):
+            fx.extract(b, p32, out=o, stream=stream)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps * len(bands))]
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for k in range(steps):
+        for i, (b, o) in enumerate(zip(bands, outs)):
+            ev[k * len(bands) + i][0].record(stream)
+            fx.extract(b, p32, out=o, stream=stream)
+            ev[k * len(bands) + i][1].record(stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    px = sum(b.numel() for b in bands)
+    diff = sum(int((a != b).sum()) for a, b in zip(outs, outs_int))
+    ms = [a.elapsed_time(b) for a, b in ev]
+    return {"gpx_s": px * steps / (e0.elapsed_time(e1) * 1e-3) / 1e9, "kernel_ms": sum(ms) / len(ms),
+            "steps": steps, "differs_from_integer_mode": diff / px,
+            "launch": "fx_extract per band, log_mode FX_LOG_FP32 (FP32 pass + wide-pass marker check)"}
 
 
 def bench_batched(fx, torch, dev, params, plan_cls):

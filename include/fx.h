@@ -32,8 +32,11 @@
  *     validation and launch errors only.
  *   - On any error nothing is launched and no output byte is written.
  *   - No call throws; no call prints.
- *   - Results are bit-identical to the definition above for every input
- *     value: integer masks, exact integer/FP32-exact arithmetic.
+ *   - In the default integer-mask mode results are bit-identical to the
+ *     definition above for every input value (exact integer / FP32-exact
+ *     arithmetic).  The optional FP32-LoG mode (fx_params.log_mode) uses
+ *     non-integer masks and FP32 responses; its results differ from the exact
+ *     definition only where a decision is within rounding of its threshold.
  */
 #ifndef FX_H
 #define FX_H
@@ -59,6 +62,12 @@ typedef enum {
 typedef enum { FX_U8 = 1, FX_U16 = 2 } fx_dtype;
 
 #define FX_MAX_HMF_LEVELS 4
+
+/* LoG evaluation modes (fx_params.log_mode). */
+typedef enum {
+  FX_LOG_INT = 0, /* integer masks, exact responses (default) */
+  FX_LOG_FP32 = 1 /* non-integer masks from Eq. 1, FP32 responses */
+} fx_log_mode;
 
 typedef struct {
   /* sizeof(fx_params); set by fx_params_default, checked by every call. */
@@ -87,6 +96,21 @@ typedef struct {
   int32_t bits;
   /* Row pitch of out_mask in bytes for fx_extract; 0 = width. */
   int64_t out_pitch;
+  /* FX_LOG_INT (default) or FX_LOG_FP32.  In FX_LOG_FP32 the masks are the
+   * mean-removed Eq. 1 samples scaled to max |w| = mask_q and rounded half
+   * away from zero to multiples of g = 2^(e - 23), 2^e the smallest power of
+   * two >= mask_q (g = 2^-14 for 512), with the centre reset to minus the sum
+   * of the other 24 (zero-sum and exact in FP32); see fx_log_mask_fp32.  Each
+   * response is evaluated in FP32 from exact ring sums R_c of the radial
+   * mask (squared radii c = 1, 2, 4, 5, 8, n_c pixels each) as
+   *   L = w1 d1 (+) w2 d2 (+) w4 d4 (+) w5 d5 (+) w8 d8,  d_c = R_c - n_c I(p),
+   * left to right with one rounding per product-add (fused multiply-add), and
+   * -0 read as +0.  The contrast test is fl(max - min) > t_zc with t_zc
+   * rounded down to FP32; the standard-deviation test stays exact.  Zero
+   * crossings and contrast then differ from the exact responses only where
+   * |L|, |L(p) + L(q)| or |max - min - t_zc| is within FP32 rounding of 0. */
+  int32_t log_mode;
+  int32_t reserved;
 } fx_params;
 
 /*
@@ -104,6 +128,15 @@ void fx_params_default(fx_params *p, fx_dtype dtype, int32_t bits);
  * mask_q < 1 or non-finite values.
  */
 fx_status fx_log_mask(double sigma, int32_t mask_q, int32_t w[25]);
+
+/*
+ * The FX_LOG_FP32 mask of one branch (see fx_params.log_mode) into w[25]
+ * (row-major).  Every weight is a multiple of 2^(e - 23) with |w| < 2^(e+1),
+ * so it is exact in FP32, and the 25 weights sum to exactly zero.  Host only.
+ * Returns FX_ERR_INVALID_ARG for sigma <= 0, mask_q < 1 or non-finite values,
+ * FX_ERR_RANGE when mask_q > 2^20.
+ */
+fx_status fx_log_mask_fp32(double sigma, int32_t mask_q, float w[25]);
 
 /*
  * One image, stateless (Sec. 4.1 flow, one fused kernel launch).

@@ -36,7 +36,7 @@ _SO = os.path.join(_BUILD, "libfx_oracle.so")
 PARAM_ORDER = (
     "sigma1", "sigma2", "mask_q", "t_zc1", "t_zc2", "t_sd5_1", "t_sd5_2",
     "t_sdmax_1", "t_sdmax_2", "t_sd3_1", "t_sd3_2", "stddev_source",
-    "hmf0", "hmf1", "hmf2", "hmf3",
+    "hmf0", "hmf1", "hmf2", "hmf3", "log_mode",
 )
 
 _lock = threading.Lock()
@@ -65,6 +65,8 @@ def _load():
             dp = ctypes.POINTER(ctypes.c_double)
             lib.fxo_log_mask.argtypes = [ctypes.c_double, ctypes.c_double, dp, dp]
             lib.fxo_log_mask.restype = ctypes.c_int
+            lib.fxo_log_mask_fp32.argtypes = [ctypes.c_double, ctypes.c_double, dp]
+            lib.fxo_log_mask_fp32.restype = ctypes.c_int
             lib.fxo_extract.argtypes = [
                 ctypes.c_void_p, ctypes.c_int, ctypes.c_longlong, ctypes.c_longlong,
                 ctypes.c_longlong, dp, ctypes.c_int, ctypes.c_longlong, ctypes.c_longlong,
@@ -88,7 +90,7 @@ def default_params(scale: float = 1.0) -> dict:
         t_zc=(4248.0 * scale, 15360.0 * scale),
         t_sd5=(6.0 * scale, 6.0 * scale), t_sdmax=(24.0 * scale, 24.0 * scale),
         t_sd3=(6.0 * scale, 6.0 * scale),
-        stddev_source=0, hmf=(5,),
+        stddev_source=0, hmf=(5,), log_mode=0,
     )
 
 
@@ -100,7 +102,7 @@ def _param_vector(p: dict) -> np.ndarray:
     v = [
         p["sigma"][0], p["sigma"][1], p["mask_q"], p["t_zc"][0], p["t_zc"][1],
         p["t_sd5"][0], p["t_sd5"][1], p["t_sdmax"][0], p["t_sdmax"][1],
-        p["t_sd3"][0], p["t_sd3"][1], p.get("stddev_source", 0), *hmf,
+        p["t_sd3"][0], p["t_sd3"][1], p.get("stddev_source", 0), *hmf, p.get("log_mode", 0),
     ]
     return np.ascontiguousarray(np.array(v, dtype=np.float64))
 
@@ -114,6 +116,15 @@ def log_mask(sigma: float, q: float = 512):
     if rc != 0:
         raise ValueError(f"fxo_log_mask rc={rc}")
     return g.reshape(5, 5), w.reshape(5, 5)
+
+
+def log_mask_fp32(sigma: float, q: float = 512) -> np.ndarray:
+    """Reading R9: the FP32-LoG mode's mask (5x5 float64, exact grid values)."""
+    w = np.zeros(25)
+    rc = _load().fxo_log_mask_fp32(float(sigma), float(q), w.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    if rc != 0:
+        raise ValueError(f"fxo_log_mask_fp32 rc={rc}")
+    return w.reshape(5, 5)
 
 
 STAGE_NAMES = ("L1", "L2", "Z1", "Z2", "C1", "C2", "S1", "S2", "M")

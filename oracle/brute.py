@@ -6,7 +6,9 @@ Where ``fx_oracle.c`` runs one pass per stage over arrays, this module writes
 each quantity of the method as a function of one pixel, evaluated on demand
 with Python integers and exact rationals:
 
-* ``L(f, x, y)``  Eq. 1 mask applied to the 5x5 neighbourhood (Sec. 4.1)
+* ``L(f, x, y)``  Eq. 1 mask applied to the 5x5 neighbourhood (Sec. 4.1);
+                  integer masks, or the FP32-LoG mode's grid masks as exact
+                  rationals
 * ``Z(f, x, y)``  zero crossing among the 4 neighbours (Sec. 3.2)
 * ``C(f, x, y)``  contrast max - min over the pixel and its 4 neighbours (Sec. 3.2)
 * ``S(f, x, y)``  standard deviation of Eq. 2 with exact rationals (Sec. 4.1)
@@ -22,6 +24,41 @@ from __future__ import annotations
 import math
 from fractions import Fraction
 from functools import lru_cache
+
+
+def _centred_samples(sigma: float):
+    samples = {}
+    for dy in range(-2, 3):
+        for dx in range(-2, 3):
+            r2 = dx * dx + dy * dy
+            s2 = sigma * sigma
+            samples[(dx, dy)] = (-1.0 / (math.pi * s2 * s2) * (1.0 - r2 / (2.0 * s2))
+                                 * math.exp(-r2 / (2.0 * s2)))
+    acc = 0.0
+    for dy in range(-2, 3):
+        for dx in range(-2, 3):
+            acc += samples[(dx, dy)]
+    mean = acc / 25.0
+    centred = {k: v - mean for k, v in samples.items()}
+    return centred, max(abs(v) for v in centred.values())
+
+
+def log_mask_fp32(sigma: float, q: float):
+    """FP32-LoG mode: the centred samples scaled to max |w| = q, rounded half
+    away from zero to multiples of 2^(e-23) (2^e the smallest power of two >= q),
+    centre reset to minus the sum of the others.  Returns dict (dx,dy)->Fraction."""
+    centred, biggest = _centred_samples(sigma)
+    e = 0
+    while 2 ** e < q:
+        e += 1
+    grid = Fraction(2) ** (e - 23)
+    w = {}
+    for k, v in centred.items():
+        t = q * v / biggest / float(grid)
+        m = int(math.floor(t + 0.5)) if t >= 0 else -int(math.floor(-t + 0.5))
+        w[k] = m * grid
+    w[(0, 0)] = -sum(v for k, v in w.items() if k != (0, 0))
+    return w
 
 
 def log_mask(sigma: float, q: float):
@@ -58,7 +95,8 @@ class Brute:
         self.height = len(img)
         self.width = len(img[0])
         self.p = params
-        self.w = [log_mask(params["sigma"][f], params["mask_q"]) for f in range(2)]
+        make = log_mask_fp32 if params.get("log_mode", 0) == 1 else log_mask
+        self.w = [make(params["sigma"][f], params["mask_q"]) for f in range(2)]
         hmf = params.get("hmf", (5,))
         if isinstance(hmf, int):
             hmf = (hmf,) if hmf else ()

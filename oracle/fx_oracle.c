@@ -15,8 +15,9 @@
  * (Sec. 4.1) -> hybrid median filter (Sec. 3.4), optionally repeated with
  * several window sizes (Sec. 4, Sec. 4.2).
  *
- * All quantities are integers below 2^53, so FP64 evaluates every stage
- * exactly; no tolerance is involved anywhere.
+ * All quantities are integers below 2^53 (in the FP32-LoG mode, R9:
+ * multiples of 2^-14 below 2^40), so FP64 evaluates every stage exactly; no
+ * tolerance is involved anywhere in the oracle.
  *
  * Readings of the paper where it is silent or garbled (numbers as in the
  * design notes):
@@ -26,11 +27,12 @@
  *       and the centre is reset to minus the sum of the other 24 weights.
  *   R2  Borders: every stage array extends outside the image by
  *       replication, S(x,y) := S(clamp(x,y)) (Sec. 4.1 gives pad sizes only).
- *   R3  Zero crossing (Sec. 3.2): with key(v) = 2|v| + [v > 0], a pixel with
- *       L != 0 is a crossing iff it has an opposite-signed 4-neighbour and
- *       its key is smaller than the key of every opposite-signed
- *       4-neighbour (ties go to the negative pixel); a pixel with L == 0 is
- *       a crossing iff L(W)L(E) < 0 or L(N)L(S) < 0.  The contrast
+ *   R3  Zero crossing (Sec. 3.2): a pixel with L != 0 is a crossing iff it
+ *       has an opposite-signed 4-neighbour and its |L| is smaller than the
+ *       |L| of every opposite-signed 4-neighbour, an exact tie going to the
+ *       negative pixel (for integer L this is key(v) = 2|v| + [v > 0]
+ *       compared strictly); a pixel with L == 0 is a crossing iff
+ *       L(W)L(E) < 0 or L(N)L(S) < 0.  The contrast
  *       max - min of L over the pixel and its 4 neighbours must exceed
  *       t_zc (strict).
  *   R4  Standard deviation (Eq. 2): unbiased s over the 5x5 window centred
@@ -46,6 +48,12 @@
  *       two diagonals (2k-1 pixels); output = median(med+, medx, centre).
  *       A list of windows applies the filter repeatedly, in order.
  *   R7  Output is a uint8 image of 0/1.
+ *   R9  FP32-LoG mode (log_mode 1, non-integer masks): the mean-removed
+ *       samples of R1, scaled to max |w| = Q, are rounded half away from zero
+ *       to multiples of g = 2^(e-23), 2^e the smallest power of two >= Q,
+ *       and the centre is reset to minus the exact sum of the other 24.  The
+ *       oracle applies these masks exactly; the library's FP32 evaluation may
+ *       differ only where a decision is within rounding of its threshold.
  */
 #include <math.h>
 #include <stdint.h>
@@ -56,7 +64,7 @@
 enum {
   P_SIGMA1 = 0, P_SIGMA2, P_Q, P_TZC1, P_TZC2, P_TSD5_1, P_TSD5_2,
   P_TSDMAX_1, P_TSDMAX_2, P_TSD3_1, P_TSD3_2, P_SOURCE,
-  P_HMF0, P_HMF1, P_HMF2, P_HMF3, P_COUNT
+  P_HMF0, P_HMF1, P_HMF2, P_HMF3, P_LOGMODE, P_COUNT
 };
 
 #define ORACLE_MAX_HMF 4
@@ -106,6 +114,35 @@ int fxo_log_mask(double sigma, double q, double *g, double *w) {
   w[12] = -others;
   if (g)
     for (int i = 0; i < 25; ++i) g[i] = samp[i];
+  return O_OK;
+}
+
+/* Reading R9: the same centred samples on the grid g = 2^(e-23) (every
+ * weight then fits the 24-bit FP32 significand), centre reset to keep the
+ * mask exactly zero-sum.  w receives the weights as doubles (exact). */
+int fxo_log_mask_fp32(double sigma, double q, double *w) {
+  if (!(sigma > 0.0) || !isfinite(sigma) || !(q >= 1.0) || !(q <= 1048576.0)) return O_BAD_ARG;
+  double samp[25], mean = 0.0;
+  for (int dy = -2; dy <= 2; ++dy)
+    for (int dx = -2; dx <= 2; ++dx) {
+      samp[(dy + 2) * 5 + (dx + 2)] = log_eq1(sigma, dx, dy);
+      mean += samp[(dy + 2) * 5 + (dx + 2)];
+    }
+  mean /= 25.0;
+  double maxabs = 0.0;
+  for (int i = 0; i < 25; ++i) {
+    double c = fabs(samp[i] - mean);
+    if (c > maxabs) maxabs = c;
+  }
+  if (!(maxabs > 0.0)) return O_BAD_ARG;
+  int e = 0;
+  while (ldexp(1.0, e) < q) ++e;
+  double grid = ldexp(1.0, e - 23), others = 0.0;
+  for (int i = 0; i < 25; ++i) {
+    w[i] = round_half_away(q * (samp[i] - mean) / maxabs / grid) * grid;
+    if (i != 12) others += w[i];
+  }
+  w[12] = -others;
   return O_OK;
 }
 
@@ -166,7 +203,11 @@ static void stage_log(const image *im, const double *w, plane *L) {
     }
 }
 
-static double zc_key(double v) { return 2.0 * fabs(v) + (v > 0.0 ? 1.0 : 0.0); }
+/* Reading R3: v (non-zero, opposite in sign to q) has the smaller magnitude;
+ * an exact tie goes to the negative pixel. */
+static int smaller_than(double v, double q) {
+  return fabs(v) < fabs(q) || (fabs(v) == fabs(q) && v < 0.0);
+}
 
 /* Sec. 3.2 with reading R3: zero crossing of L at every pixel of Z. */
 static void stage_zero_crossing(plane *L, plane *Z) {
@@ -181,7 +222,7 @@ static void stage_zero_crossing(plane *L, plane *Z) {
         for (int k = 0; k < 4; ++k)
           if (v * nb[k] < 0.0) {
             any = 1;
-            if (!(zc_key(v) < zc_key(nb[k]))) smallest = 0;
+            if (!smaller_than(v, nb[k])) smallest = 0;
           }
         z = any && smallest;
       } else {
@@ -298,10 +339,15 @@ int fxo_extract(const void *img, int elem, long long W, long long H, long long p
   for (int i = 0; i < P_COUNT; ++i)
     if (isnan(prm[i])) return O_BAD_ARG;
 
+  int log_mode = (int)prm[P_LOGMODE];
+  if (log_mode != 0 && log_mode != 1) return O_BAD_ARG;
   image im = {(const uint8_t *)img, elem, W, H, pitch};
   double w[2][25];
-  for (int f = 0; f < 2; ++f)
-    if (fxo_log_mask(prm[P_SIGMA1 + f], prm[P_Q], NULL, w[f]) != O_OK) return O_BAD_ARG;
+  for (int f = 0; f < 2; ++f) {
+    int rc0 = log_mode == 0 ? fxo_log_mask(prm[P_SIGMA1 + f], prm[P_Q], NULL, w[f])
+                            : fxo_log_mask_fp32(prm[P_SIGMA1 + f], prm[P_Q], w[f]);
+    if (rc0 != O_OK) return O_BAD_ARG;
+  }
 
   /* Rows each stage needs so that the output rows are complete. */
   long long r_s = r_m;                      /* S, C, Z(as used), E, M */

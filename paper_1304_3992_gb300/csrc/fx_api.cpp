@@ -30,6 +30,40 @@ int32_t contrast_threshold(double T) {
   return static_cast<int32_t>(fl);
 }
 
+// Eq. 1 (Sec. 3.1) sampled on x, y in {-2..2}, minus its mean; big = max |g|.
+bool centred_eq1(double sigma, double g[25], double *big) {
+  if (!(sigma > 0.0) || !std::isfinite(sigma)) return false;
+  const double s2 = sigma * sigma;
+  const double k = -1.0 / (kPi * s2 * s2);
+  double total = 0.0;
+  for (int i = 0; i < 25; ++i) {
+    const double dx = i % 5 - 2, dy = i / 5 - 2;
+    const double t = (dx * dx + dy * dy) / (2.0 * s2);
+    g[i] = k * (1.0 - t) * std::exp(-t);
+    total += g[i];
+  }
+  const double mean = total / 25.0;
+  *big = 0.0;
+  for (int i = 0; i < 25; ++i) {
+    g[i] -= mean;
+    *big = std::fmax(*big, std::fabs(g[i]));
+  }
+  return *big > 0.0 && std::isfinite(*big);
+}
+
+// Largest float <= t (t itself when it is a float).
+float float_at_or_below(double t) {
+  float f = static_cast<float>(t);
+  if (static_cast<double>(f) > t) f = std::nextafter(f, -INFINITY);
+  return f;
+}
+
+// Ring index (squared radius 0, 1, 2, 4, 5, 8 -> 0..5) of tap i of a 5x5 mask.
+int ring_of(int i) {
+  const int dx = i % 5 - 2, dy = i / 5 - 2, r2 = dx * dx + dy * dy;
+  return r2 == 0 ? 0 : r2 == 1 ? 1 : r2 == 2 ? 2 : r2 == 4 ? 3 : r2 == 5 ? 4 : 5;
+}
+
 }  // namespace
 
 fx_status make_kparams(const fx_params *p, int32_t maxval, KParams *kp) {
@@ -40,7 +74,9 @@ fx_status make_kparams(const fx_params *p, int32_t maxval, KParams *kp) {
   for (const double *d : dv)
     if (std::isnan(*d)) return FX_ERR_INVALID_ARG;
   if (p->stddev_source != 0 && p->stddev_source != 1) return FX_ERR_INVALID_ARG;
+  if (p->log_mode != FX_LOG_INT && p->log_mode != FX_LOG_FP32) return FX_ERR_INVALID_ARG;
   kp->source = p->stddev_source;
+  kp->f32log = p->log_mode == FX_LOG_FP32;
   for (int i = 0; i < FX_MAX_HMF_LEVELS; ++i) {
     int k = p->hmf[i];
     if (k == 0) break;
@@ -61,39 +97,58 @@ fx_status make_kparams(const fx_params *p, int32_t maxval, KParams *kp) {
     // the construction keeps Eq. 1's radial symmetry; the ring form relies on it
     int64_t pos = 0;
     for (int i = 0; i < 25; ++i) {
-      int dx = i % 5 - 2, dy = i / 5 - 2, r2 = dx * dx + dy * dy;
-      int c = r2 == 0 ? 0 : r2 == 1 ? 1 : r2 == 2 ? 2 : r2 == 4 ? 3 : r2 == 5 ? 4 : 5;
-      if (kp->w[f][i] != kp->ring[f][c]) return FX_ERR_UNSUPPORTED;
+      if (kp->w[f][i] != kp->ring[f][ring_of(i)]) return FX_ERR_UNSUPPORTED;
       if (kp->w[f][i] > 0) pos += kp->w[f][i];
     }
     if (pos > splus) splus = pos;
+    if (kp->f32log) {  // FP32-LoG mode: the ring weights are the non-integer mask's
+      float wf[25];
+      st = fx_log_mask_fp32(p->sigma[f], p->mask_q, wf);
+      if (st != FX_OK) return st;
+      for (int c = 0; c < 6; ++c) kp->ringf[f][c] = wf[(ry[c] + 2) * 5 + rx[c] + 2];
+      for (int i = 0; i < 25; ++i)
+        if (wf[i] != kp->ringf[f][ring_of(i)]) return FX_ERR_UNSUPPORTED;
+      kp->tzf[f] = float_at_or_below(p->t_zc[f]);
+    }
     kp->tzc[f] = contrast_threshold(p->t_zc[f]);
     kp->tsd5[f] = sd_threshold(p->t_sd5[f], 25.0);
     kp->tsdmax[f] = sd_threshold(p->t_sdmax[f], 25.0);
     kp->tsd3[f] = sd_threshold(p->t_sd3[f], 9.0);
   }
   kp->splus = splus;
-  // |L| <= maxval * splus for every partial sum; the contrast needs twice that.
-  if (2 * static_cast<int64_t>(maxval) * splus >= INT32_MAX) return FX_ERR_RANGE;
-  // FP32 path: partial sums of L below 2^24 and D below 2^32 (values <= 4095).
-  int64_t fb = splus > 0 ? ((1LL << 24) - 1) / splus : 4095;
-  if (fb > 4095) fb = 4095;
-  kp->fbound = static_cast<int32_t>(fb);
+  if (kp->f32log) {
+    // FP32 responses need no range condition; the FP32 pass keeps 32-bit
+    // standard-deviation sums for values <= 4095 and the wide pass takes the rest.
+    kp->fbound = 4095;
+  } else {
+    // |L| <= maxval * splus for every partial sum; the contrast needs twice that.
+    if (2 * static_cast<int64_t>(maxval) * splus >= INT32_MAX) return FX_ERR_RANGE;
+    // FP32-exact path: partial sums of L below 2^24 and D below 2^32 (values <= 4095).
+    int64_t fb = splus > 0 ? ((1LL << 24) - 1) / splus : 4095;
+    if (fb > 4095) fb = 4095;
+    kp->fbound = static_cast<int32_t>(fb);
+  }
+  auto tt = [](int64_t t) -> uint32_t {  // D > t  <=>  D >= t + 1 (D < 2^32)
+    if (t < 0) return 0u;
+    if (t >= 0xFFFFFFFFLL) return 0xFFFFFFFFu;
+    return static_cast<uint32_t>(t + 1);
+  };
   for (int f = 0; f < 2; ++f) {
-    // max - min < 2^25 on the FP32 path; tzc + 1 must be exact or out of reach
-    const int64_t t1 = static_cast<int64_t>(kp->tzc[f]) + 1;
-    if (t1 <= (1LL << 24)) kp->tzc1f[f] = static_cast<float>(t1);
-    else if (t1 >= (1LL << 25)) kp->tzc1f[f] = 33554432.0f;
-    else kp->fbound = -1;
-    auto tt = [](int64_t t) -> uint32_t {  // D > t  <=>  D >= t + 1 (D < 2^32)
-      if (t < 0) return 0u;
-      if (t >= 0xFFFFFFFFLL) return 0xFFFFFFFFu;
-      return static_cast<uint32_t>(t + 1);
-    };
+    if (kp->f32log) {
+      // fl(max - min) - tzc1f < 0  <=>  fl(max - min) <= tzf  (tzc1f = next float above tzf)
+      kp->tzc1f[f] = std::nextafter(kp->tzf[f], INFINITY);
+      kp->fixzero[f] = kp->ringf[f][5] > 0.0f ? 0 : 1;
+    } else {
+      // max - min < 2^25 on the FP32-exact path; tzc + 1 must be exact or out of reach
+      const int64_t t1 = static_cast<int64_t>(kp->tzc[f]) + 1;
+      if (t1 <= (1LL << 24)) kp->tzc1f[f] = static_cast<float>(t1);
+      else if (t1 >= (1LL << 25)) kp->tzc1f[f] = 33554432.0f;
+      else kp->fbound = -1;
+      kp->fixzero[f] = kp->ring[f][5] > 0 ? 0 : 1;
+    }
     kp->tt5[f] = tt(kp->tsd5[f]);
     kp->ttmax[f] = tt(kp->tsdmax[f]);
     kp->tt3[f] = tt(kp->tsd3[f]);
-    kp->fixzero[f] = kp->ring[f][5] > 0 ? 0 : 1;
   }
   kp->sd_same = kp->tsd5[0] == kp->tsd5[1] && kp->tsdmax[0] == kp->tsdmax[1] && kp->tsd3[0] == kp->tsd3[1];
   return FX_OK;
@@ -163,29 +218,40 @@ void fx_params_default(fx_params *p, fx_dtype dtype, int32_t bits) {
 // Eq. 1 sampled on the 5x5 grid; mean removed; scaled so that max |w| = Q;
 // rounded half away from zero; centre tap reset to make the mask zero-sum.
 fx_status fx_log_mask(double sigma, int32_t mask_q, int32_t w[25]) {
-  if (!w || !(sigma > 0.0) || !std::isfinite(sigma) || mask_q < 1) return FX_ERR_INVALID_ARG;
-  const double s2 = sigma * sigma;
-  const double k = -1.0 / (kPi * s2 * s2);
-  double g[25], total = 0.0;
-  for (int i = 0; i < 25; ++i) {
-    const double dx = i % 5 - 2, dy = i / 5 - 2;
-    const double t = (dx * dx + dy * dy) / (2.0 * s2);
-    g[i] = k * (1.0 - t) * std::exp(-t);
-    total += g[i];
-  }
-  const double mean = total / 25.0;
-  double big = 0.0;
-  for (double gi : g) big = std::fmax(big, std::fabs(gi - mean));
-  if (!(big > 0.0) || !std::isfinite(big)) return FX_ERR_INVALID_ARG;
+  double g[25], big = 0.0;
+  if (!w || mask_q < 1 || !centred_eq1(sigma, g, &big)) return FX_ERR_INVALID_ARG;
   int64_t rest = 0;
   for (int i = 0; i < 25; ++i) {
-    const double r = round_half_away(static_cast<double>(mask_q) * (g[i] - mean) / big);
+    const double r = round_half_away(static_cast<double>(mask_q) * g[i] / big);
     if (!(std::fabs(r) < 1e9)) return FX_ERR_RANGE;
     w[i] = static_cast<int32_t>(r);
     if (i != 12) rest += w[i];
   }
   if (rest > INT32_MAX || rest < -INT32_MAX) return FX_ERR_RANGE;
   w[12] = static_cast<int32_t>(-rest);
+  return FX_OK;
+}
+
+// The same samples on the grid 2^(e-23), 2^e the smallest power of two >= Q:
+// every weight then has at most 24 significant bits (exact in FP32) and the
+// centre, minus the exact sum of the other 24, keeps the mask zero-sum.
+fx_status fx_log_mask_fp32(double sigma, int32_t mask_q, float w[25]) {
+  double g[25], big = 0.0;
+  if (!w || mask_q < 1 || !centred_eq1(sigma, g, &big)) return FX_ERR_INVALID_ARG;
+  if (mask_q > (1 << 20)) return FX_ERR_RANGE;
+  int e = 0;
+  while ((int64_t{1} << e) < mask_q) ++e;
+  const double grid = std::ldexp(1.0, e - 23), lim = std::ldexp(1.0, e + 1);
+  double v[25], rest = 0.0;
+  for (int i = 0; i < 25; ++i) {
+    v[i] = round_half_away(static_cast<double>(mask_q) * g[i] / big / grid) * grid;
+    if (i != 12) rest += v[i];  // exact: multiples of grid below 2^(e+6)
+  }
+  v[12] = -rest;
+  for (int i = 0; i < 25; ++i) {
+    if (!(std::fabs(v[i]) < lim)) return FX_ERR_RANGE;
+    w[i] = static_cast<float>(v[i]);
+  }
   return FX_OK;
 }
 

@@ -84,6 +84,7 @@ __global__ void __launch_bounds__(256) batch_kernel_general(const unsigned char 
   }
 }
 
+template <bool kF32Log>
 __global__ void __launch_bounds__(32 * kWarpsPerCta, 3) batch_kernel_fast(const unsigned char *table,
                                                                       unsigned long long *counter, int *status,
                                                                       const __grid_constant__ KParams kp8,
@@ -106,13 +107,15 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta, 3) batch_kernel_fast(const 
     const ImageView v = view_of(b);
     const long long local = u - b.unit_begin;
     const int64_t ux = local % b.units_x, uy = local / b.units_x;
-    if (b.elem == 1) fast_unit<uint8_t>(v, kp8, ux, uy, hdr->unit_w, hdr->unit_h, warp_words(words));
-    else fast_unit<uint16_t>(v, kp16, ux, uy, hdr->unit_w, hdr->unit_h, warp_words(words));
+    if (b.elem == 1) fast_unit<uint8_t, kF32Log>(v, kp8, ux, uy, hdr->unit_w, hdr->unit_h, warp_words(words));
+    else fast_unit<uint16_t, kF32Log>(v, kp16, ux, uy, hdr->unit_w, hdr->unit_h, warp_words(words));
   }
 }
 
 // Second pass of the streaming path: every warp walks the units with a static
-// stride and recomputes, on the integer path, the strips the first pass marked.
+// stride and recomputes, on the integer (or wide FP32-LoG) path, the strips
+// the first pass marked.
+template <bool kF32Log>
 __global__ void __launch_bounds__(32 * kWarpsPerCta, 3) batch_kernel_redo(const unsigned char *table,
                                                                       unsigned long long *, int *,
                                                                       const __grid_constant__ KParams kp8,
@@ -130,11 +133,21 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta, 3) batch_kernel_redo(const 
     const int64_t ux = local % b.units_x, uy = local / b.units_x;
     if (b.elem == 1) {
       if (kp8.fbound < 0 || kp8.fbound < 255)
-        fast_unit_redo<uint8_t>(v, kp8, ux, uy, hdr->unit_w, hdr->unit_h, warp_words(words));
+        fast_unit_redo<uint8_t, kF32Log>(v, kp8, ux, uy, hdr->unit_w, hdr->unit_h, warp_words(words));
     } else {
-      fast_unit_redo<uint16_t>(v, kp16, ux, uy, hdr->unit_w, hdr->unit_h, warp_words(words));
+      fast_unit_redo<uint16_t, kF32Log>(v, kp16, ux, uy, hdr->unit_w, hdr->unit_h, warp_words(words));
     }
   }
+}
+
+// The streaming kernels of a plan's LoG mode.
+const void *fast_kernel_of(const KParams &kp) {
+  return kp.f32log ? reinterpret_cast<const void *>(&batch_kernel_fast<true>)
+                   : reinterpret_cast<const void *>(&batch_kernel_fast<false>);
+}
+const void *redo_kernel_of(const KParams &kp) {
+  return kp.f32log ? reinterpret_cast<const void *>(&batch_kernel_redo<true>)
+                   : reinterpret_cast<const void *>(&batch_kernel_redo<false>);
 }
 
 }  // namespace
@@ -185,8 +198,7 @@ size_t unit_smem(const fx_plan *p) {
 // persistent kernel.  The table copy has a fixed size so the graph never changes.
 fx_status build_graph(fx_plan *p, int i) {
   p->smem = unit_smem(p);
-  const void *fn = p->fast ? reinterpret_cast<const void *>(&batch_kernel_fast)
-                           : reinterpret_cast<const void *>(&batch_kernel_general);
+  const void *fn = p->fast ? fast_kernel_of(p->kp8) : reinterpret_cast<const void *>(&batch_kernel_general);
   if (!p->fast &&  // the streaming kernels use static shared memory only
       cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) != cudaSuccess)
     return FX_ERR_CUDA;
@@ -224,7 +236,7 @@ fx_status build_graph(fx_plan *p, int i) {
   if (e == cudaSuccess) e = cudaGraphAddKernelNode(&n_kern, g, &n_zero, 1, &kn);
   if (e == cudaSuccess && p->fast) {  // integer redo pass of the streaming path
     cudaKernelNodeParams kr = kn;
-    kr.func = reinterpret_cast<void *>(&batch_kernel_redo);
+    kr.func = const_cast<void *>(redo_kernel_of(p->kp8));
     kr.sharedMemBytes = 0;
     cudaGraphNode_t n_redo;
     e = cudaGraphAddKernelNode(&n_redo, g, &n_kern, 1, &kr);
@@ -421,7 +433,7 @@ fx_status fx_plan_autotune(fx_plan *p, const fx_image_desc *descs, int32_t n, vo
       if (!p->fast && (uw != kDefaultUnitW || uh != kDefaultUnitH)) continue;
       if ((st = fx_plan_set_tile(p, uw, uh, cps)) != FX_OK) break;
       int occ = 0;
-      if (p->fast) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batch_kernel_fast, 32 * kWarpsPerCta, 0);
+      if (p->fast) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fast_kernel_of(p->kp8), 32 * kWarpsPerCta, 0);
       else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batch_kernel_general, 256, p->smem);
       if (occ < cps) continue;
       float t_best = 1e30f;

@@ -4,7 +4,7 @@
 namespace fx {
 namespace {
 
-template <typename T, bool kRedoPass>
+template <typename T, bool kRedoPass, bool kF32Log>
 __global__ void __launch_bounds__(32 * kWarpsPerCta, 3) stream_kernel(const __grid_constant__ ImageView v,
                                                                   const __grid_constant__ KParams kp,
                                                                   int64_t units_x, int64_t units, int uh) {
@@ -12,19 +12,26 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta, 3) stream_kernel(const __gr
   const int64_t unit = static_cast<int64_t>(blockIdx.x) * kWarpsPerCta + (threadIdx.x >> 5);
   if (unit >= units) return;  // whole warps only
   if constexpr (kRedoPass)
-    fast_unit_redo<T>(v, kp, unit % units_x, unit / units_x, kDefaultUnitW, uh, warp_words(words));
+    fast_unit_redo<T, kF32Log>(v, kp, unit % units_x, unit / units_x, kDefaultUnitW, uh, warp_words(words));
   else
-    fast_unit<T>(v, kp, unit % units_x, unit / units_x, kDefaultUnitW, uh, warp_words(words));
+    fast_unit<T, kF32Log>(v, kp, unit % units_x, unit / units_x, kDefaultUnitW, uh, warp_words(words));
+}
+
+template <typename T, bool kF32Log>
+void launch_mode(const ImageView &v, const KParams &kp, cudaStream_t s, int64_t blocks, int64_t units_x,
+                 int64_t units, int uh) {
+  const unsigned g = static_cast<unsigned>(blocks);
+  if (kp.fbound >= 0) stream_kernel<T, false, kF32Log><<<g, 32 * kWarpsPerCta, 0, s>>>(v, kp, units_x, units, uh);
+  // the second pass recomputes the strips the first one marked (all when fbound < 0)
+  if (kp.fbound < 0 || kp.fbound < (sizeof(T) == 1 ? 255 : 65535))
+    stream_kernel<T, true, kF32Log><<<g, 32 * kWarpsPerCta, 0, s>>>(v, kp, units_x, units, uh);
 }
 
 template <typename T>
 cudaError_t launch_t(const ImageView &v, const KParams &kp, cudaStream_t s, int64_t blocks, int64_t units_x,
                      int64_t units, int uh) {
-  if (kp.fbound >= 0)
-    stream_kernel<T, false><<<static_cast<unsigned>(blocks), 32 * kWarpsPerCta, 0, s>>>(v, kp, units_x, units, uh);
-  // the integer pass recomputes the strips the FP32 pass marked (all when fbound < 0)
-  if (kp.fbound < 0 || kp.fbound < (sizeof(T) == 1 ? 255 : 65535))
-    stream_kernel<T, true><<<static_cast<unsigned>(blocks), 32 * kWarpsPerCta, 0, s>>>(v, kp, units_x, units, uh);
+  if (kp.f32log) launch_mode<T, true>(v, kp, s, blocks, units_x, units, uh);
+  else launch_mode<T, false>(v, kp, s, blocks, units_x, units, uh);
   return cudaGetLastError();
 }
 

@@ -94,12 +94,20 @@ __device__ __forceinline__ uint32_t maj5(const uint32_t x[5]) {
 // Pack the sign bit of v into an accumulator (shift-left insertion).
 __device__ __forceinline__ void put(uint32_t &acc, uint32_t v) { acc = __funnelshift_l(v, acc, 1); }
 
-template <bool kInt>
+// Arithmetic of a strip.  kModeF32 / kModeInt: integer masks, exact FP32 or
+// int32 / int64 arithmetic.  kModeF32Log / kModeF32LogWide: the FP32-LoG mode
+// (non-integer masks, L rounded in FP32), with 32-bit or 64-bit sums for the
+// exact standard-deviation test.
+enum : int { kModeF32 = 0, kModeInt = 1, kModeF32Log = 2, kModeF32LogWide = 3 };
+
+template <int kMode>
 struct Ar;
 
 // FP32 path: values <= fbound, every intermediate an exact FP32 integer.
 template <>
-struct Ar<false> {
+struct Ar<kModeF32> {
+  static constexpr bool kRel = false;     // L from the ring sums R_c directly
+  static constexpr bool kChecked = true;  // values above fbound send the strip to the redo pass
   using V = float;
   using Q = uint32_t;
   static __device__ __forceinline__ V cvt(uint32_t u) { return __uint_as_float(0x4B000000u | u) - 8388608.0f; }
@@ -135,7 +143,9 @@ struct Ar<false> {
 
 // Integer path: any uint16 value (|L| < 2^30 by the plan's range check).
 template <>
-struct Ar<true> {
+struct Ar<kModeInt> {
+  static constexpr bool kRel = false;
+  static constexpr bool kChecked = false;
   using V = int32_t;
   using Q = uint64_t;
   static __device__ __forceinline__ V cvt(uint32_t u) { return static_cast<int32_t>(u); }
@@ -157,9 +167,35 @@ struct Ar<true> {
   static __device__ __forceinline__ V fix(const KParams &, int, V x) { return x; }
 };
 
-template <typename T, bool kInt>
+// FP32-LoG mode, values <= fbound (32-bit standard-deviation sums).  L is
+// evaluated from d_c = R_c - n_c I(p) (exact), so flat neighbourhoods give an
+// exact 0 and mirrored neighbourhoods exactly opposite responses.
+template <>
+struct Ar<kModeF32Log> : Ar<kModeF32> {
+  static constexpr bool kRel = true;
+};
+
+// FP32-LoG mode, any uint16 value: the same FP32 responses, 64-bit D.
+template <>
+struct Ar<kModeF32LogWide> : Ar<kModeF32> {
+  static constexpr bool kRel = true;
+  static constexpr bool kChecked = false;
+  using Q = uint64_t;
+  static __device__ __forceinline__ Q sq(uint32_t u) { return static_cast<uint64_t>(u) * u; }
+  static __device__ __forceinline__ uint32_t sdpass(const KParams &kp, int f, V A3, V A5, Q Q3, Q Q5) {
+    // A3, A5 are exact integers below 2^21
+    const int64_t a3 = static_cast<int64_t>(__float_as_uint(A3 + 8388608.0f) - 0x4B000000u);
+    const int64_t a5 = static_cast<int64_t>(__float_as_uint(A5 + 8388608.0f) - 0x4B000000u);
+    const int64_t d3 = 9 * static_cast<int64_t>(Q3) - a3 * a3;
+    const int64_t d5 = 25 * static_cast<int64_t>(Q5) - a5 * a5;
+    const bool pass = d5 > kp.tsdmax[f] ? d3 > kp.tsd3[f] : d5 > kp.tsd5[f];
+    return pass ? 0x80000000u : 0u;
+  }
+};
+
+template <typename T, int kMode>
 struct Strip {
-  using A = Ar<kInt>;
+  using A = Ar<kMode>;
   using V = typename A::V;
   using Q = typename A::Q;
 
@@ -201,7 +237,7 @@ struct Strip {
     W = v.width;
     H = v.height;
     xs = X0 - kLeftHalo;
-    check = !kInt && kp.fbound < (sizeof(T) == 1 ? 255 : 65535);
+    check = A::kChecked && kp.fbound < (sizeof(T) == 1 ? 255 : 65535);
     border = xs < 0 || xs + kWinCols > W;
     const uintptr_t base = reinterpret_cast<uintptr_t>(v.img);
     vload = (base % (2 * sizeof(T)) == 0) && (v.pitch % (2 * sizeof(T)) == 0) && (xs % 2 == 0);
@@ -339,15 +375,31 @@ struct Strip {
       const V R4 = h2_[c0][j] + (f_[m2][j] + fn[j]);
       const V R5 = (h2_[m1][j] + h2_[p1][j]) + (h1_[m2][j] + h1n[j]);
       const V R8 = h2_[m2][j] + h2n[j];
+      if constexpr (A::kRel) {
+        // FP32-LoG: one rounding per product-add, in the order of the ring radii
+        const float d1 = __fmaf_rn(-4.0f, R0, R1), d2 = __fmaf_rn(-4.0f, R0, R2);
+        const float d4 = __fmaf_rn(-4.0f, R0, R4), d5 = __fmaf_rn(-8.0f, R0, R5);
+        const float d8 = __fmaf_rn(-4.0f, R0, R8);
 #pragma unroll
-      for (int f = 0; f < 2; ++f) {
-        V l = A::w(kp, f, 0) * R0;
-        l = l + A::w(kp, f, 1) * R1;
-        l = l + A::w(kp, f, 2) * R2;
-        l = l + A::w(kp, f, 3) * R4;
-        l = l + A::w(kp, f, 4) * R5;
-        l = l + A::w(kp, f, 5) * R8;  // positive outer weight last: no -0 (else fix)
-        L_[f][c0][j] = A::fix(kp, f, l);
+        for (int f = 0; f < 2; ++f) {
+          float l = __fmul_rn(A::w(kp, f, 1), d1);
+          l = __fmaf_rn(A::w(kp, f, 2), d2, l);
+          l = __fmaf_rn(A::w(kp, f, 3), d4, l);
+          l = __fmaf_rn(A::w(kp, f, 4), d5, l);
+          l = __fmaf_rn(A::w(kp, f, 5), d8, l);  // positive last weight: no -0 (else fix)
+          L_[f][c0][j] = A::fix(kp, f, l);
+        }
+      } else {
+#pragma unroll
+        for (int f = 0; f < 2; ++f) {
+          V l = A::w(kp, f, 0) * R0;
+          l = l + A::w(kp, f, 1) * R1;
+          l = l + A::w(kp, f, 2) * R2;
+          l = l + A::w(kp, f, 3) * R4;
+          l = l + A::w(kp, f, 4) * R5;
+          l = l + A::w(kp, f, 5) * R8;  // positive outer weight last: no -0 (else fix)
+          L_[f][c0][j] = A::fix(kp, f, l);
+        }
       }
       const V A3 = R0 + R1 + R2;
       const V A5 = A3 + R4 + R5 + R8;
@@ -569,21 +621,24 @@ constexpr int kStripWords = 20;
 using StripWords = uint32_t[kWarpsPerCta][kStripWords][32];
 __device__ __forceinline__ uint32_t (*warp_words(StripWords &w))[32] { return w[(threadIdx.x >> 5) % kWarpsPerCta]; }
 
-template <typename T>
+// kF32Log selects the FP32-LoG mode (KParams::f32log) at compile time.
+template <typename T, bool kF32Log>
 __device__ __forceinline__ void fast_unit(const ImageView &v, const KParams &kp, int64_t ux, int64_t uy, int,
                                           int uh, uint32_t (*words)[32]) {
-  static_assert(st::Strip<T, false>::kWords == kStripWords, "shared word layout");
+  constexpr int kMode = kF32Log ? st::kModeF32Log : st::kModeF32;
+  static_assert(st::Strip<T, kMode>::kWords == kStripWords, "shared word layout");
   if (kp.fbound < 0) return;
   const int64_t X0 = ux * st::kOutCols;
   const int64_t Y0 = v.y_begin + uy * uh;
   const int64_t Y1 = Y0 + uh < v.y_end ? Y0 + uh : v.y_end;
-  st::Strip<T, false> s(v, kp, X0, Y0, Y1, words);
+  st::Strip<T, kMode> s(v, kp, X0, Y0, Y1, words);
   if (!s.run() && (threadIdx.x & 31) == 0) *unit_marker(v, ux, uy, uh) = kRedo;
 }
 
-template <typename T>
+template <typename T, bool kF32Log>
 __device__ __forceinline__ void fast_unit_redo(const ImageView &v, const KParams &kp, int64_t ux, int64_t uy,
                                                int, int uh, uint32_t (*words)[32]) {
+  constexpr int kMode = kF32Log ? st::kModeF32LogWide : st::kModeInt;
   if (kp.fbound >= 0) {
     uint8_t mark = 0;
     if ((threadIdx.x & 31) == 0) mark = *unit_marker(v, ux, uy, uh);
@@ -592,7 +647,7 @@ __device__ __forceinline__ void fast_unit_redo(const ImageView &v, const KParams
   const int64_t X0 = ux * st::kOutCols;
   const int64_t Y0 = v.y_begin + uy * uh;
   const int64_t Y1 = Y0 + uh < v.y_end ? Y0 + uh : v.y_end;
-  st::Strip<T, true> s(v, kp, X0, Y0, Y1, words);
+  st::Strip<T, kMode> s(v, kp, X0, Y0, Y1, words);
   s.run();
 }
 

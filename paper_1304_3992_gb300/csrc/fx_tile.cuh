@@ -12,8 +12,9 @@
 //
 // This kernel handles every parameter combination (any number of median
 // passes, either standard-deviation source, any dtype) in exact integer
-// arithmetic.  The streaming kernel in fx_stream.cu is the fast path for the
-// default configuration; both must agree bit for bit.
+// arithmetic, or with FP32 responses in the FP32-LoG mode.  The streaming
+// kernel in fx_stream.cu is the fast path for the default configuration;
+// both must agree bit for bit in either mode.
 #include <cstdint>
 
 #pragma once
@@ -77,6 +78,55 @@ __device__ __forceinline__ int64_t zc_key(int64_t v) { return 2 * (v < 0 ? -v : 
 
 __device__ __forceinline__ bool opposite(int64_t a, int64_t b) { return (a < 0 && b > 0) || (a > 0 && b < 0); }
 
+// FP32-LoG mode (KParams::f32log): L is stored as float bits in the same arrays.
+__device__ __forceinline__ bool opposite_f(float a, float b) { return (a < 0.f && b > 0.f) || (a > 0.f && b < 0.f); }
+// c beats an opposite-signed q: smaller magnitude, ties to the negative pixel (reading R3)
+__device__ __forceinline__ bool beats_f(float c, float q) {
+  return fabsf(c) < fabsf(q) || (fabsf(c) == fabsf(q) && c < 0.f);
+}
+
+// Ring index (squared radius 0, 1, 2, 4, 5, 8 -> 0..5) of the offset (dx, dy).
+__device__ __forceinline__ int ring_index(int dx, int dy) {
+  const int r2 = dx * dx + dy * dy;
+  return r2 == 0 ? 0 : r2 == 1 ? 1 : r2 == 2 ? 2 : r2 == 4 ? 3 : r2 == 5 ? 4 : 5;
+}
+
+// FP32-LoG response from exact ring sums: the operations of the streaming
+// kernel, in its order (d_c = R_c - n_c R0, products added left to right).
+__device__ __forceinline__ float log_f32(const KParams &kp, int f, const int32_t R[6]) {
+  const float d1 = static_cast<float>(R[1] - 4 * R[0]), d2 = static_cast<float>(R[2] - 4 * R[0]);
+  const float d4 = static_cast<float>(R[3] - 4 * R[0]), d5 = static_cast<float>(R[4] - 8 * R[0]);
+  const float d8 = static_cast<float>(R[5] - 4 * R[0]);
+  float l = __fmul_rn(kp.ringf[f][1], d1);
+  l = __fmaf_rn(kp.ringf[f][2], d2, l);
+  l = __fmaf_rn(kp.ringf[f][3], d4, l);
+  l = __fmaf_rn(kp.ringf[f][4], d5, l);
+  l = __fmaf_rn(kp.ringf[f][5], d8, l);
+  return kp.fixzero[f] ? __fadd_rn(l, 0.0f) : l;
+}
+
+// Contrast test of Sec. 3.2 over the pixel and its 4 neighbours (clamped
+// coordinates): max - min > t_zc, or fl(max - min) > tzf in the FP32-LoG mode.
+__device__ __forceinline__ bool contrast_pass(const KParams &kp, int f, const Arr<int32_t> &L, int64_t xc, int64_t yc,
+                                              int64_t xw, int64_t xe, int64_t yn, int64_t ys) {
+  const int32_t v[5] = {L.at_clamped(xc, yc), L.at_clamped(xw, yc), L.at_clamped(xe, yc), L.at_clamped(xc, yn),
+                        L.at_clamped(xc, ys)};
+  if (kp.f32log) {
+    float mx = __int_as_float(v[0]), mn = mx;
+    for (int k = 1; k < 5; ++k) {
+      mx = fmaxf(mx, __int_as_float(v[k]));
+      mn = fminf(mn, __int_as_float(v[k]));
+    }
+    return __fsub_rn(mx, mn) > kp.tzf[f];
+  }
+  int32_t mx = v[0], mn = v[0];
+  for (int k = 1; k < 5; ++k) {
+    mx = max(mx, v[k]);
+    mn = min(mn, v[k]);
+  }
+  return mx - mn > kp.tzc[f];
+}
+
 // One TW x TH output tile whose top-left output pixel is (x0, y0).  All NT
 // threads of the CTA must call it; smem holds general_smem_bytes(kp) bytes.
 template <typename T>
@@ -114,6 +164,16 @@ __device__ void general_tile(const ImageView &v, const KParams &kp, int64_t x0, 
   // a2: the two LoG responses (Eq. 1 masks on the 5x5 neighbourhood).
   for (int i = threadIdx.x; i < area(R.l); i += NT) {
     int64_t xc = clampll(L[0].ox + i % L[0].w, 0, W - 1), yc = clampll(L[0].oy + i / L[0].w, 0, H - 1);
+    if (kp.f32log) {
+      int32_t R[6] = {0, 0, 0, 0, 0, 0};  // exact ring sums (< 2^20)
+      for (int dy = -2; dy <= 2; ++dy) {
+        int64_t yy = clampll(yc + dy, 0, H - 1);
+        for (int dx = -2; dx <= 2; ++dx) R[ring_index(dx, dy)] += I.at_clamped(clampll(xc + dx, 0, W - 1), yy);
+      }
+      L[0].p[i] = __float_as_int(log_f32(kp, 0, R));
+      L[1].p[i] = __float_as_int(log_f32(kp, 1, R));
+      continue;
+    }
     int32_t acc0 = 0, acc1 = 0;
     for (int dy = -2; dy <= 2; ++dy) {
       int64_t yy = clampll(yc + dy, 0, H - 1);
@@ -134,6 +194,25 @@ __device__ void general_tile(const ImageView &v, const KParams &kp, int64_t x0, 
     int64_t xw = clampll(xc - 1, 0, W - 1), xe = clampll(xc + 1, 0, W - 1);
     int64_t yn = clampll(yc - 1, 0, H - 1), ys = clampll(yc + 1, 0, H - 1);
     for (int f = 0; f < 2; ++f) {
+      if (kp.f32log) {
+        const float c = __int_as_float(L[f].at_clamped(xc, yc));
+        const float nb[4] = {__int_as_float(L[f].at_clamped(xw, yc)), __int_as_float(L[f].at_clamped(xe, yc)),
+                             __int_as_float(L[f].at_clamped(xc, yn)), __int_as_float(L[f].at_clamped(xc, ys))};
+        bool z;
+        if (c != 0.f) {
+          bool any = false, smallest = true;
+          for (int k = 0; k < 4; ++k)
+            if (opposite_f(c, nb[k])) {
+              any = true;
+              if (!beats_f(c, nb[k])) smallest = false;
+            }
+          z = any && smallest;
+        } else {
+          z = opposite_f(nb[0], nb[1]) || opposite_f(nb[2], nb[3]);
+        }
+        Z[f].p[i] = z;
+        continue;
+      }
       int64_t c = L[f].at_clamped(xc, yc);
       int64_t nb[4] = {L[f].at_clamped(xw, yc), L[f].at_clamped(xe, yc), L[f].at_clamped(xc, yn),
                        L[f].at_clamped(xc, ys)};
@@ -178,15 +257,7 @@ __device__ void general_tile(const ImageView &v, const KParams &kp, int64_t x0, 
     }
     for (int f = 0; f < 2; ++f) {
       if (!Z[f].at_clamped(xc, yc)) continue;
-      int32_t c = L[f].at_clamped(xc, yc);
-      int32_t nb[4] = {L[f].at_clamped(xw, yc), L[f].at_clamped(xe, yc), L[f].at_clamped(xc, yn),
-                       L[f].at_clamped(xc, ys)};
-      int32_t mx = c, mn = c;
-      for (int k = 0; k < 4; ++k) {
-        mx = max(mx, nb[k]);
-        mn = min(mn, nb[k]);
-      }
-      if (!(mx - mn > kp.tzc[f])) continue;
+      if (!contrast_pass(kp, f, L[f], xc, yc, xw, xe, yn, ys)) continue;
       if (kp.source == 1) {
         s5 = q5 = s3 = q3 = 0;
         for (int dy = -2; dy <= 2; ++dy) {

@@ -15,6 +15,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libfx.so")
 
 FX_U8, FX_U16 = 1, 2
+FX_LOG_INT, FX_LOG_FP32 = 0, 1
 MAX_HMF = 4
 STATUS = {0: "FX_OK", 1: "FX_ERR_INVALID_ARG", 2: "FX_ERR_UNSUPPORTED", 3: "FX_ERR_RANGE",
           4: "FX_ERR_CUDA", 5: "FX_ERR_NOMEM", 6: "FX_ERR_BUDGET", 7: "FX_ERR_TIMEOUT"}
@@ -39,6 +40,8 @@ class Params(ctypes.Structure):
         ("hmf", ctypes.c_int32 * MAX_HMF),
         ("bits", ctypes.c_int32),
         ("out_pitch", ctypes.c_int64),
+        ("log_mode", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
     ]
 
 
@@ -61,6 +64,7 @@ _lib = None
 _SIGNATURES = {
     "fx_params_default": (None, [ctypes.POINTER(Params), ctypes.c_int, ctypes.c_int32]),
     "fx_log_mask": (ctypes.c_int, [ctypes.c_double, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]),
+    "fx_log_mask_fp32": (ctypes.c_int, [ctypes.c_double, ctypes.c_int32, ctypes.POINTER(ctypes.c_float)]),
     "fx_extract": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
                                   ctypes.c_int, ctypes.POINTER(Params), ctypes.c_void_p, ctypes.c_void_p]),
     "fx_plan_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(Params),
@@ -131,7 +135,8 @@ def _stream_ptr(stream) -> int:
 def make_params(dtype: int = FX_U16, bits: int = 0, **overrides) -> Params:
     """fx_params_default(dtype, bits) with optional overrides.  Accepts the keys
     sigma, mask_q, t_zc, t_sd5, t_sdmax, t_sd3 (pairs), stddev_source,
-    hmf (int or sequence of windows), bits, out_pitch."""
+    hmf (int or sequence of windows), bits, out_pitch, log_mode (FX_LOG_INT
+    or FX_LOG_FP32)."""
     p = Params()
     load().fx_params_default(ctypes.byref(p), dtype, bits)
     for k, v in overrides.items():
@@ -142,7 +147,7 @@ def make_params(dtype: int = FX_U16, bits: int = 0, **overrides) -> Params:
             seq = tuple(x for x in seq if x) + (0,) * MAX_HMF
             for i in range(MAX_HMF):
                 p.hmf[i] = int(seq[i])
-        elif k in ("mask_q", "stddev_source", "bits", "out_pitch"):
+        elif k in ("mask_q", "stddev_source", "bits", "out_pitch", "log_mode"):
             setattr(p, k, int(v))
         else:
             raise KeyError(k)
@@ -157,6 +162,13 @@ def params_from_dict(d: dict, dtype: int = FX_U16) -> Params:
 def log_mask(sigma: float, q: int = 512):
     w = (ctypes.c_int32 * 25)()
     _check(load().fx_log_mask(float(sigma), int(q), w), "fx_log_mask")
+    return [list(w[i * 5:(i + 1) * 5]) for i in range(5)]
+
+
+def log_mask_fp32(sigma: float, q: int = 512):
+    """The FP32-LoG mode's non-integer mask (5x5 list of floats)."""
+    w = (ctypes.c_float * 25)()
+    _check(load().fx_log_mask_fp32(float(sigma), int(q), w), "fx_log_mask_fp32")
     return [list(w[i * 5:(i + 1) * 5]) for i in range(5)]
 
 
