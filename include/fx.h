@@ -142,7 +142,8 @@ fx_status fx_log_mask_fp32(double sigma, int32_t mask_q, float w[25]);
  * One image, stateless (Sec. 4.1 flow, one fused kernel launch).
  *   img          device pointer to row 0; aligned to the element size
  *   width,height pixels, both >= 1
- *   pitch_bytes  distance between image rows, >= width*elem, multiple of elem
+ *   pitch_bytes  distance between image rows, >= width*elem, multiple of elem,
+ *                below 2^32
  *   dtype        FX_U8 or FX_U16
  *   params       NULL = fx_params_default(dtype, 0)
  *   out_mask     device pointer, height rows of params->out_pitch (or width)

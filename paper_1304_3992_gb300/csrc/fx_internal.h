@@ -67,6 +67,7 @@ struct ImageView {
 
 cudaError_t launch_tile_general(const ImageView &v, const KParams &kp, cudaStream_t s);
 bool fast_path_supported(const KParams &kp);
+bool pair_loads_ok(const ImageView &v);
 cudaError_t launch_fast(const ImageView &v, const KParams &kp, cudaStream_t s);
 cudaError_t launch_extract(const ImageView &v, const KParams &kp, cudaStream_t s);
 

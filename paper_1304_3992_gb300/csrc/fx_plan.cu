@@ -27,6 +27,9 @@ struct BatchImage {
 
 struct BatchHeader {
   int64_t total_units;
+  // streaming path: units [0, pair_units) belong to images read with one aligned
+  // load per lane (listed first), the rest to images read pixel by pixel
+  int64_t pair_units;
   int32_t n;
   int32_t unit_w, unit_h;  // unit shape in output pixels
   int32_t pad;
@@ -84,7 +87,10 @@ __global__ void __launch_bounds__(256) batch_kernel_general(const unsigned char 
   }
 }
 
-template <bool kF32Log>
+// kPair: the units [0, pair_units) from counter[0]; otherwise [pair_units,
+// total_units) from counter[1].  The two run as consecutive launches, so each
+// kernel holds one strip loop per dtype.
+template <bool kF32Log, bool kPair>
 __global__ void __launch_bounds__(32 * kWarpsPerCta, 3) batch_kernel_fast(const unsigned char *table,
                                                                       unsigned long long *counter, int *status,
                                                                       const __grid_constant__ KParams kp8,
@@ -92,13 +98,14 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta, 3) batch_kernel_fast(const 
   __shared__ StripWords words;
   const BatchHeader *hdr = reinterpret_cast<const BatchHeader *>(table);
   const BatchImage *ims = reinterpret_cast<const BatchImage *>(table + sizeof(BatchHeader));
-  const long long total = hdr->total_units;
+  const long long first = kPair ? 0 : hdr->pair_units;
+  const long long end = kPair ? hdr->pair_units : hdr->total_units;
   const int lane = threadIdx.x & 31;
   for (;;) {
     unsigned long long got = 0;
-    if (lane == 0) got = atomicAdd(counter, 1ULL);
-    const long long u = static_cast<long long>(__shfl_sync(0xffffffffu, got, 0));
-    if (u >= total) break;
+    if (lane == 0) got = atomicAdd(counter + (kPair ? 0 : 1), 1ULL);
+    const long long u = first + static_cast<long long>(__shfl_sync(0xffffffffu, got, 0));
+    if (u >= end) break;
     const BatchImage &b = ims[find_image(ims, hdr->n, u)];
     if (b.units_x <= 0 || (b.elem != 1 && b.elem != 2)) {
       if (lane == 0) atomicOr(status, kStatusBadDescriptor);
@@ -107,8 +114,8 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta, 3) batch_kernel_fast(const 
     const ImageView v = view_of(b);
     const long long local = u - b.unit_begin;
     const int64_t ux = local % b.units_x, uy = local / b.units_x;
-    if (b.elem == 1) fast_unit<uint8_t, kF32Log>(v, kp8, ux, uy, hdr->unit_w, hdr->unit_h, warp_words(words));
-    else fast_unit<uint16_t, kF32Log>(v, kp16, ux, uy, hdr->unit_w, hdr->unit_h, warp_words(words));
+    if (b.elem == 1) fast_unit<uint8_t, kF32Log, kPair>(v, kp8, ux, uy, hdr->unit_w, hdr->unit_h, warp_words(words));
+    else fast_unit<uint16_t, kF32Log, kPair>(v, kp16, ux, uy, hdr->unit_w, hdr->unit_h, warp_words(words));
   }
 }
 
@@ -141,9 +148,12 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta, 3) batch_kernel_redo(const 
 }
 
 // The streaming kernels of a plan's LoG mode.
-const void *fast_kernel_of(const KParams &kp) {
-  return kp.f32log ? reinterpret_cast<const void *>(&batch_kernel_fast<true>)
-                   : reinterpret_cast<const void *>(&batch_kernel_fast<false>);
+const void *fast_kernel_of(const KParams &kp, bool pair) {
+  if (kp.f32log)
+    return pair ? reinterpret_cast<const void *>(&batch_kernel_fast<true, true>)
+                : reinterpret_cast<const void *>(&batch_kernel_fast<true, false>);
+  return pair ? reinterpret_cast<const void *>(&batch_kernel_fast<false, true>)
+              : reinterpret_cast<const void *>(&batch_kernel_fast<false, false>);
 }
 const void *redo_kernel_of(const KParams &kp) {
   return kp.f32log ? reinterpret_cast<const void *>(&batch_kernel_redo<true>)
@@ -198,7 +208,7 @@ size_t unit_smem(const fx_plan *p) {
 // persistent kernel.  The table copy has a fixed size so the graph never changes.
 fx_status build_graph(fx_plan *p, int i) {
   p->smem = unit_smem(p);
-  const void *fn = p->fast ? fast_kernel_of(p->kp8) : reinterpret_cast<const void *>(&batch_kernel_general);
+  const void *fn = p->fast ? fast_kernel_of(p->kp8, true) : reinterpret_cast<const void *>(&batch_kernel_general);
   if (!p->fast &&  // the streaming kernels use static shared memory only
       cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) != cudaSuccess)
     return FX_ERR_CUDA;
@@ -216,9 +226,9 @@ fx_status build_graph(fx_plan *p, int i) {
   ms.dst = p->d_counter;
   ms.value = 0;
   ms.elementSize = 4;
-  ms.width = 2;
+  ms.width = 4;  // both queue counters
   ms.height = 1;
-  ms.pitch = 8;
+  ms.pitch = 16;
   const unsigned char *tab = p->d_table;
   unsigned long long *ctr = p->d_counter;
   int *stp = p->d_status;
@@ -234,12 +244,17 @@ fx_status build_graph(fx_plan *p, int i) {
   cudaError_t e = cudaGraphAddMemcpyNode(&n_copy, g, nullptr, 0, &cp);
   if (e == cudaSuccess) e = cudaGraphAddMemsetNode(&n_zero, g, &n_copy, 1, &ms);
   if (e == cudaSuccess) e = cudaGraphAddKernelNode(&n_kern, g, &n_zero, 1, &kn);
-  if (e == cudaSuccess && p->fast) {  // integer redo pass of the streaming path
+  if (e == cudaSuccess && p->fast) {
+    // images read pixel by pixel, then the integer (or wide) redo pass
+    cudaKernelNodeParams kb = kn;
+    kb.func = const_cast<void *>(fast_kernel_of(p->kp8, false));
+    cudaGraphNode_t n_kb;
+    e = cudaGraphAddKernelNode(&n_kb, g, &n_kern, 1, &kb);
     cudaKernelNodeParams kr = kn;
     kr.func = const_cast<void *>(redo_kernel_of(p->kp8));
     kr.sharedMemBytes = 0;
     cudaGraphNode_t n_redo;
-    e = cudaGraphAddKernelNode(&n_redo, g, &n_kern, 1, &kr);
+    if (e == cudaSuccess) e = cudaGraphAddKernelNode(&n_redo, g, &n_kb, 1, &kr);
   }
   if (e == cudaSuccess) e = cudaGraphInstantiate(&p->graph[i], g, 0);
   cudaGraphDestroy(g);
@@ -260,14 +275,25 @@ fx_status fill_table(fx_plan *p, unsigned char *h, const fx_image_desc *d, int32
   BatchImage *ims = reinterpret_cast<BatchImage *>(h + sizeof(BatchHeader));
   const int uw = p->fast ? p->unit_w : gen::TW, uh = p->fast ? p->unit_h : gen::TH;
   const int uwx = p->fast ? kDefaultUnitW : gen::TW;  // output columns per unit
-  int64_t total = 0;
+  int64_t total = 0, pair_units = 0;
+  // On the streaming path the queue runs through the images in four groups:
+  // one aligned load per lane (uint16, then uint8), then pixel by pixel (uint16,
+  // then uint8).  The first two groups go to one kernel and the last two to
+  // the next, and within a kernel the warps of an SM mostly run the loop of
+  // one dtype at a time, which keeps the instruction working set small.
+  int32_t slot = 0;
+  for (int pass = 0; pass < (p->fast ? 4 : 1); ++pass)
   for (int32_t i = 0; i < n; ++i) {
     const int64_t op = d[i].out_pitch ? d[i].out_pitch : d[i].width;
+    const int64_t elem = d[i].dtype == FX_U8 ? 1 : 2;
+    const bool pair = p->fast && reinterpret_cast<uintptr_t>(d[i].img) % (2 * elem) == 0 &&
+                      d[i].pitch_bytes % (2 * elem) == 0 && d[i].width % 2 == 0;
+    if (p->fast && (pair != (pass < 2) || (d[i].dtype == FX_U8) != (pass % 2 == 1))) continue;
     fx_status st = check_image(d[i].img, d[i].width, d[i].height, d[i].pitch_bytes, d[i].dtype,
                                d[i].out_mask, op);
     if (st != FX_OK) return st;
     if (d[i].dtype == FX_U16 && p->st16 != FX_OK) return p->st16;
-    BatchImage &b = ims[i];
+    BatchImage &b = ims[slot++];
     b.img = d[i].img;
     b.width = d[i].width;
     b.height = d[i].height;
@@ -279,7 +305,9 @@ fx_status fill_table(fx_plan *p, unsigned char *h, const fx_image_desc *d, int32
     b.units_x = (b.width + uwx - 1) / uwx;
     b.unit_begin = total;
     total += b.units_x * ((b.height + uh - 1) / uh);
+    if (pass < 2) pair_units = total;
   }
+  if (slot != n) return FX_ERR_INVALID_ARG;  // every descriptor belongs to exactly one group
   // outputs must not overlap each other (inputs were checked per descriptor)
   for (int32_t i = 0; i < n; ++i)
     for (int32_t j = i + 1; j < n; ++j) {
@@ -290,6 +318,7 @@ fx_status fill_table(fx_plan *p, unsigned char *h, const fx_image_desc *d, int32
       if ((a0 < b1 && b0 < a1) || (a0 < c1 && c0 < a1) || (b0 < e1 && e0 < b1)) return FX_ERR_INVALID_ARG;
     }
   hdr->total_units = total;
+  hdr->pair_units = p->fast ? pair_units : total;
   hdr->n = n;
   hdr->unit_w = uw;
   hdr->unit_h = uh;
@@ -342,7 +371,7 @@ fx_status fx_plan_create(fx_plan **out, const fx_params *params, int32_t max_ima
     return FX_ERR_CUDA;
   }
   bool ok = cudaMalloc(&p->d_table, table_bytes(max_images)) == cudaSuccess &&
-            cudaMalloc(&p->d_counter, 8) == cudaSuccess && cudaMalloc(&p->d_status, 4) == cudaSuccess &&
+            cudaMalloc(&p->d_counter, 16) == cudaSuccess && cudaMalloc(&p->d_status, 4) == cudaSuccess &&
             cudaMemset(p->d_status, 0, 4) == cudaSuccess;
   for (int i = 0; i < 2 && ok; ++i) {
     ok = cudaMallocHost(&p->h_table[i], table_bytes(max_images)) == cudaSuccess &&
@@ -433,7 +462,7 @@ fx_status fx_plan_autotune(fx_plan *p, const fx_image_desc *descs, int32_t n, vo
       if (!p->fast && (uw != kDefaultUnitW || uh != kDefaultUnitH)) continue;
       if ((st = fx_plan_set_tile(p, uw, uh, cps)) != FX_OK) break;
       int occ = 0;
-      if (p->fast) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fast_kernel_of(p->kp8), 32 * kWarpsPerCta, 0);
+      if (p->fast) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fast_kernel_of(p->kp8, true), 32 * kWarpsPerCta, 0);
       else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batch_kernel_general, 256, p->smem);
       if (occ < cps) continue;
       float t_best = 1e30f;

@@ -4,7 +4,7 @@
 namespace fx {
 namespace {
 
-template <typename T, bool kRedoPass, bool kF32Log>
+template <typename T, bool kRedoPass, bool kF32Log, bool kPair>
 __global__ void __launch_bounds__(32 * kWarpsPerCta, 3) stream_kernel(const __grid_constant__ ImageView v,
                                                                   const __grid_constant__ KParams kp,
                                                                   int64_t units_x, int64_t units, int uh) {
@@ -14,17 +14,22 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta, 3) stream_kernel(const __gr
   if constexpr (kRedoPass)
     fast_unit_redo<T, kF32Log>(v, kp, unit % units_x, unit / units_x, kDefaultUnitW, uh, warp_words(words));
   else
-    fast_unit<T, kF32Log>(v, kp, unit % units_x, unit / units_x, kDefaultUnitW, uh, warp_words(words));
+    fast_unit<T, kF32Log, kPair>(v, kp, unit % units_x, unit / units_x, kDefaultUnitW, uh, warp_words(words));
 }
 
 template <typename T, bool kF32Log>
 void launch_mode(const ImageView &v, const KParams &kp, cudaStream_t s, int64_t blocks, int64_t units_x,
                  int64_t units, int uh) {
   const unsigned g = static_cast<unsigned>(blocks);
-  if (kp.fbound >= 0) stream_kernel<T, false, kF32Log><<<g, 32 * kWarpsPerCta, 0, s>>>(v, kp, units_x, units, uh);
+  if (kp.fbound >= 0) {
+    if (pair_loads_ok(v))
+      stream_kernel<T, false, kF32Log, true><<<g, 32 * kWarpsPerCta, 0, s>>>(v, kp, units_x, units, uh);
+    else
+      stream_kernel<T, false, kF32Log, false><<<g, 32 * kWarpsPerCta, 0, s>>>(v, kp, units_x, units, uh);
+  }
   // the second pass recomputes the strips the first one marked (all when fbound < 0)
   if (kp.fbound < 0 || kp.fbound < (sizeof(T) == 1 ? 255 : 65535))
-    stream_kernel<T, true, kF32Log><<<g, 32 * kWarpsPerCta, 0, s>>>(v, kp, units_x, units, uh);
+    stream_kernel<T, true, kF32Log, false><<<g, 32 * kWarpsPerCta, 0, s>>>(v, kp, units_x, units, uh);
 }
 
 template <typename T>
@@ -40,6 +45,13 @@ cudaError_t launch_t(const ImageView &v, const KParams &kp, cudaStream_t s, int6
 // The streaming kernel covers the default configuration: image source for the
 // standard deviation and at most one median pass.
 bool fast_path_supported(const KParams &kp) { return kp.source == 0 && kp.nhmf <= 1; }
+
+// One aligned load per lane and row: base and pitch multiples of two pixels,
+// even width (so every lane's clamped columns lie in one aligned pair).
+bool pair_loads_ok(const ImageView &v) {
+  const int64_t two = 2 * static_cast<int64_t>(v.elem);
+  return reinterpret_cast<uintptr_t>(v.img) % two == 0 && v.pitch % two == 0 && v.width % 2 == 0;
+}
 
 cudaError_t launch_fast(const ImageView &v, const KParams &kp, cudaStream_t s) {
   const int uh = kDefaultUnitH;

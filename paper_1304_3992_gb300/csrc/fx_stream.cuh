@@ -193,7 +193,12 @@ struct Ar<kModeF32LogWide> : Ar<kModeF32> {
   }
 };
 
-template <typename T, int kMode>
+// kPair: one aligned load of the lane's two pixels per row (images whose base
+// and pitch are multiples of two pixels and whose width is even); otherwise
+// two single-pixel loads.  Either way every load is unconditional and lands in
+// a ring slot that is read four steps later, so loads overlap the arithmetic;
+// the clamped (replicated, reading R2) columns are selected when a row is used.
+template <typename T, int kMode, bool kPair>
 struct Strip {
   using A = Ar<kMode>;
   using V = typename A::V;
@@ -203,7 +208,7 @@ struct Strip {
   const KParams &kp;
   int64_t X0, Y0, Y1, xs, W, H;
   int lane;
-  bool check, border, vload, vstore;
+  bool check, border, vstore;
   int bl_lane, bl_slot, br_lane, br_slot;
   uint32_t outmask_l, outmask_r;  // this lane's slots left of / right of the image (M0 << j)
 
@@ -214,7 +219,7 @@ struct Strip {
   V L_[2][4][2];
   V LW_[2][4], LE_[2][4];
   uint32_t S_[2][4][2];
-  uint32_t raw_[4];
+  uint32_t raw_[4], raw1_[4];  // loaded pixels of rows t..t+3 (raw1_: second pixel, !kPair)
   uint32_t vmax_;
   uint32_t acc_[12];
   // Words of earlier blocks, touched once per 16 rows, live in shared memory:
@@ -224,11 +229,11 @@ struct Strip {
   static constexpr int kBlk = 0, kPneg = 12, kPpos = 14, kPsS = 16, kMA = 18, kMB = 19, kWords = 20;
   __device__ __forceinline__ uint32_t &blk(int i) { return sw_[kBlk + i][lane]; }
 
-  // load state: rows relative to Y0
-  int32_t rlo, rhi, Hrel, Y0rel;
-  const unsigned char *rowY0;
-  bool cload;      // this lane's 2 columns are inside the image and aligned
-  int32_t xcl[2];  // clamped columns (only when !cload)
+  // load state: rows relative to Y0; p0_ / p1_ address row rbase
+  int32_t rlo, rhi, Hrel, Y0rel, rbase;
+  const unsigned char *p0_, *p1_;
+  uint32_t pitch32;
+  uint32_t sel_;  // kPair: byte selector taking the clamped columns out of the loaded pair
 
   __device__ Strip(const ImageView &v_, const KParams &kp_, int64_t x0, int64_t y0, int64_t y1,
                    uint32_t (*words)[32])
@@ -239,8 +244,6 @@ struct Strip {
     xs = X0 - kLeftHalo;
     check = A::kChecked && kp.fbound < (sizeof(T) == 1 ? 255 : 65535);
     border = xs < 0 || xs + kWinCols > W;
-    const uintptr_t base = reinterpret_cast<uintptr_t>(v.img);
-    vload = (base % (2 * sizeof(T)) == 0) && (v.pitch % (2 * sizeof(T)) == 0) && (xs % 2 == 0);
     vstore = (reinterpret_cast<uintptr_t>(v.out) % 2 == 0) && (v.out_pitch % 2 == 0) && (xs % 2 == 0);
     const int64_t bl = -xs, br = W - 1 - xs;  // window columns of image columns 0 and W-1
     bl_lane = bl > 0 ? static_cast<int>(bl >> 1) : 0;
@@ -258,10 +261,23 @@ struct Strip {
     rhi = static_cast<int32_t>(hi - Y0);
     Hrel = static_cast<int32_t>(H - Y0);
     Y0rel = static_cast<int32_t>(Y0 < (1 << 30) ? Y0 : (1 << 30));
-    cload = vload && x >= 0 && x + 1 < W;
-    for (int j = 0; j < 2; ++j) xcl[j] = static_cast<int32_t>(x + j < 0 ? 0 : (x + j >= W ? W - 1 : x + j));
-    rowY0 = static_cast<const unsigned char *>(v.img) + (Y0 - v.row0) * v.pitch +
-            (cload ? x * static_cast<int64_t>(sizeof(T)) : 0);
+    // rows a unit reads are >= Y0 - 8; offsets from there fit 32 bits times the pitch
+    rbase = rlo > -8 ? rlo : -8;
+    pitch32 = static_cast<uint32_t>(v.pitch);
+    const unsigned char *base = static_cast<const unsigned char *>(v.img) + (Y0 + rbase - v.row0) * v.pitch;
+    const int64_t d0 = x < 0 ? 0 : (x >= W ? W - 1 : x), d1 = x + 1 < 0 ? 0 : (x + 1 >= W ? W - 1 : x + 1);
+    if constexpr (kPair) {
+      // the even pair (cb, cb + 1) inside the row that holds both clamped columns
+      const int64_t cb = (d0 < W - 2 ? d0 : W - 2) & ~int64_t{1};
+      p0_ = p1_ = base + cb * static_cast<int64_t>(sizeof(T));
+      const uint32_t h0 = static_cast<uint32_t>(d0 - cb), h1 = static_cast<uint32_t>(d1 - cb);
+      if constexpr (sizeof(T) == 2) sel_ = (h0 ? 0x32u : 0x10u) | ((h1 ? 0x32u : 0x10u) << 8);
+      else sel_ = h0 | 0x40u | (h1 << 8) | 0x4000u;
+    } else {
+      p0_ = base + d0 * static_cast<int64_t>(sizeof(T));
+      p1_ = base + d1 * static_cast<int64_t>(sizeof(T));
+      sel_ = 0x5410u;
+    }
     vmax_ = 0;
     for (int i = 0; i < 12; ++i) acc_[i] = 0;
     for (int i = 0; i < kWords; ++i) sw_[i][lane] = 0;
@@ -275,28 +291,31 @@ struct Strip {
         S_[0][s][j] = S_[1][s][j] = 0;
       }
       LW_[0][s] = LW_[1][s] = LE_[0][s] = LE_[1][s] = V(0);
-      raw_[s] = 0;
+      raw_[s] = raw1_[s] = 0;
     }
   }
 
-  // Row t (relative to Y0) into raw slot S as a 16-bit pair (column 0 low).
-  // Rows outside the image clamp to it (reading R2); rows outside the buffer
-  // (a row band) clamp to the buffer: they feed only rows that are not stored.
+  // Row t (relative to Y0) into ring slot S.  Rows outside the image clamp to
+  // it (reading R2); rows outside the buffer (a row band) clamp to the buffer:
+  // they feed only rows that are not stored.
   template <int S>
   __device__ __forceinline__ void load_row(int32_t tr) {
     const int32_t yr = tr < rlo ? rlo : (tr > rhi ? rhi : tr);
-    const unsigned char *row = rowY0 + static_cast<int64_t>(yr) * v.pitch;
-    if (cload) {
-      if constexpr (sizeof(T) == 2) {
-        raw_[S] = __ldg(reinterpret_cast<const uint32_t *>(row));
-      } else {
-        raw_[S] = __byte_perm(static_cast<uint32_t>(__ldg(reinterpret_cast<const uint16_t *>(row))), 0, 0x4140);
-      }
+    const uint64_t off = static_cast<uint64_t>(static_cast<uint32_t>(yr - rbase)) * pitch32;
+    if constexpr (kPair) {
+      if constexpr (sizeof(T) == 2) raw_[S] = __ldg(reinterpret_cast<const uint32_t *>(p0_ + off));
+      else raw_[S] = __ldg(reinterpret_cast<const uint16_t *>(p0_ + off));
     } else {
-      const uint32_t u0 = static_cast<uint32_t>(__ldg(reinterpret_cast<const T *>(row) + xcl[0]));
-      const uint32_t u1 = static_cast<uint32_t>(__ldg(reinterpret_cast<const T *>(row) + xcl[1]));
-      raw_[S] = u0 | (u1 << 16);
+      raw_[S] = __ldg(reinterpret_cast<const T *>(p0_ + off));
+      raw1_[S] = __ldg(reinterpret_cast<const T *>(p1_ + off));
     }
+  }
+
+  // The lane's two pixels of the row in slot S as a 16-bit pair (column 0 low).
+  template <int S>
+  __device__ __forceinline__ uint32_t pixels() const {
+    if constexpr (kPair) return __byte_perm(raw_[S], 0, sel_);
+    else return __byte_perm(raw_[S], raw1_[S], 0x5410);
   }
 
   // Replace the values of window columns outside the image by the value of the
@@ -326,7 +345,7 @@ struct Strip {
 
   template <int S>
   __device__ __forceinline__ void step(int32_t t) {  // t relative to Y0, S = t & 3
-    const uint32_t w = raw_[S];
+    const uint32_t w = pixels<S>();
     load_row<S>(t + 4);  // four rows ahead, into the slot just read
     if (check) vmax_ = __vmaxu2(vmax_, w);
     const uint32_t hl = __shfl_up_sync(kFull, w, 1);    // columns -2, -1
@@ -622,16 +641,16 @@ using StripWords = uint32_t[kWarpsPerCta][kStripWords][32];
 __device__ __forceinline__ uint32_t (*warp_words(StripWords &w))[32] { return w[(threadIdx.x >> 5) % kWarpsPerCta]; }
 
 // kF32Log selects the FP32-LoG mode (KParams::f32log) at compile time.
-template <typename T, bool kF32Log>
+template <typename T, bool kF32Log, bool kPair>
 __device__ __forceinline__ void fast_unit(const ImageView &v, const KParams &kp, int64_t ux, int64_t uy, int,
                                           int uh, uint32_t (*words)[32]) {
   constexpr int kMode = kF32Log ? st::kModeF32Log : st::kModeF32;
-  static_assert(st::Strip<T, kMode>::kWords == kStripWords, "shared word layout");
+  static_assert(st::Strip<T, kMode, kPair>::kWords == kStripWords, "shared word layout");
   if (kp.fbound < 0) return;
   const int64_t X0 = ux * st::kOutCols;
   const int64_t Y0 = v.y_begin + uy * uh;
   const int64_t Y1 = Y0 + uh < v.y_end ? Y0 + uh : v.y_end;
-  st::Strip<T, kMode> s(v, kp, X0, Y0, Y1, words);
+  st::Strip<T, kMode, kPair> s(v, kp, X0, Y0, Y1, words);
   if (!s.run() && (threadIdx.x & 31) == 0) *unit_marker(v, ux, uy, uh) = kRedo;
 }
 
@@ -647,7 +666,7 @@ __device__ __forceinline__ void fast_unit_redo(const ImageView &v, const KParams
   const int64_t X0 = ux * st::kOutCols;
   const int64_t Y0 = v.y_begin + uy * uh;
   const int64_t Y1 = Y0 + uh < v.y_end ? Y0 + uh : v.y_end;
-  st::Strip<T, kMode> s(v, kp, X0, Y0, Y1, words);
+  st::Strip<T, kMode, false> s(v, kp, X0, Y0, Y1, words);
   s.run();
 }
 
