@@ -147,7 +147,7 @@ fx_status fx_log_mask_fp32(double sigma, int32_t mask_q, float w[25]);
  *   dtype        FX_U8 or FX_U16
  *   params       NULL = fx_params_default(dtype, 0)
  *   out_mask     device pointer, height rows of params->out_pitch (or width)
- *                bytes; must not overlap the image
+ *                bytes, out_pitch below 2^32; must not overlap the image
  * Errors: FX_ERR_INVALID_ARG, FX_ERR_RANGE, FX_ERR_UNSUPPORTED, FX_ERR_CUDA.
  * Thread-safe; allocates nothing.
  */

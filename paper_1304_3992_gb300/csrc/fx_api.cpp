@@ -161,7 +161,7 @@ fx_status check_image(const void *img, int64_t width, int64_t height, int64_t pi
   const int64_t elem = dtype == FX_U8 ? 1 : 2;
   if (width < 1 || height < 1 || width > (1LL << 30) || height > (1LL << 30)) return FX_ERR_INVALID_ARG;
   if (pitch_bytes < width * elem || pitch_bytes % elem != 0 || pitch_bytes > 0xFFFFFFFFLL) return FX_ERR_INVALID_ARG;
-  if (out_pitch < width) return FX_ERR_INVALID_ARG;
+  if (out_pitch < width || out_pitch > 0xFFFFFFFFLL) return FX_ERR_INVALID_ARG;
   if (reinterpret_cast<uintptr_t>(img) % elem != 0) return FX_ERR_INVALID_ARG;
   const uintptr_t a0 = reinterpret_cast<uintptr_t>(img);
   const uintptr_t a1 = a0 + (height - 1) * pitch_bytes + width * elem;

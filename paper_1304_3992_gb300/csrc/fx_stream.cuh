@@ -550,20 +550,33 @@ struct Strip {
     const int64_t x = xs + 2 * lane;
     const bool lane_out = lane >= 3 && lane < 29 && x < W;
     if (!lane_out) return;
-    const bool full = vstore && x + 1 < W;
     const int64_t ybase = Y0 - 3 + 16 * b;
+    // rows [ybase + rlo, ybase + rhi) of this block belong to the unit
+    const int64_t lo64 = Y0 - ybase, hi64 = Y1 - ybase;
+    const int rlo = lo64 < 0 ? 0 : static_cast<int>(lo64), rhi = hi64 > 16 ? 16 : static_cast<int>(hi64);
+    if (rhi <= rlo) return;
+    const uint32_t rows = ((1u << rhi) - 1u) & ~((1u << rlo) - 1u);
     uint8_t *dst = v.out + (ybase - v.y_begin) * v.out_pitch + x;
+    const uint32_t op = static_cast<uint32_t>(v.out_pitch);
+    if (vstore && x + 1 < W) {
+      // two rows at a time: their 4 bits (h bits 28-2r .. 31-2r) spread to 4
+      // bytes by one multiply, then one 16-bit store per row
 #pragma unroll
-    for (int r = 0; r < 16; ++r, dst += v.out_pitch) {
-      const int64_t y = ybase + r;
-      if (y < Y0 || y >= Y1) continue;
-      const uint32_t pr = (h >> (30 - 2 * r)) & 0x3u;
-      const uint32_t bytes = (pr | (pr << 7)) & 0x0101u;
-      if (full) {
-        *reinterpret_cast<uint16_t *>(dst) = static_cast<uint16_t>(bytes);
-      } else {
-        dst[0] = static_cast<uint8_t>(bytes & 1u);
-        if (x + 1 < W) dst[1] = static_cast<uint8_t>(bytes >> 8);
+      for (int r = 0; r < 16; r += 2) {
+        const uint32_t q = (h >> (28 - 2 * r)) & 0xFu;
+        const uint32_t e = (q * 0x00204081u) & 0x01010101u;  // bit k of q -> byte k
+        if (rows & (1u << r)) *reinterpret_cast<uint16_t *>(dst + static_cast<uint64_t>(r) * op) = static_cast<uint16_t>(e >> 16);
+        if (rows & (2u << r))
+          *reinterpret_cast<uint16_t *>(dst + static_cast<uint64_t>(r + 1) * op) = static_cast<uint16_t>(e);
+      }
+    } else {
+#pragma unroll
+      for (int r = 0; r < 16; ++r) {
+        if (!(rows & (1u << r))) continue;
+        const uint32_t pr = (h >> (30 - 2 * r)) & 0x3u;
+        uint8_t *d = dst + static_cast<uint64_t>(r) * op;
+        d[0] = static_cast<uint8_t>(pr & 1u);
+        if (x + 1 < W) d[1] = static_cast<uint8_t>(pr >> 1);
       }
     }
   }
