@@ -137,14 +137,12 @@ fx_status make_kparams(const fx_params *p, int32_t maxval, KParams *kp) {
     if (kp->f32log) {
       // fl(max - min) - tzc1f < 0  <=>  fl(max - min) <= tzf  (tzc1f = next float above tzf)
       kp->tzc1f[f] = std::nextafter(kp->tzf[f], INFINITY);
-      kp->fixzero[f] = kp->ringf[f][5] > 0.0f ? 0 : 1;
     } else {
       // max - min < 2^25 on the FP32-exact path; tzc + 1 must be exact or out of reach
       const int64_t t1 = static_cast<int64_t>(kp->tzc[f]) + 1;
       if (t1 <= (1LL << 24)) kp->tzc1f[f] = static_cast<float>(t1);
       else if (t1 >= (1LL << 25)) kp->tzc1f[f] = 33554432.0f;
       else kp->fbound = -1;
-      kp->fixzero[f] = kp->ring[f][5] > 0 ? 0 : 1;
     }
     kp->tt5[f] = tt(kp->tsd5[f]);
     kp->ttmax[f] = tt(kp->tsdmax[f]);

@@ -36,7 +36,6 @@ struct KParams {
   // 32-bit standard-deviation tests for the FP32 path: s > T  <=>  D >= tt.
   uint32_t tt5[2], ttmax[2], tt3[2];
   int32_t sd_same;   // both branches use the same standard-deviation thresholds
-  int32_t fixzero[2];  // last weight of the sum not positive: canonicalise -0 after it
   // FP32-LoG mode (fx_params.log_mode): ringf holds the non-integer mask's ring
   // weights and L is evaluated in FP32 from d_c = R_c - n_c I(p); the contrast
   // test is fl(max - min) > tzf (t_zc rounded down to FP32).

@@ -90,7 +90,7 @@ __global__ void __launch_bounds__(256) batch_kernel_general(const unsigned char 
 // kPair: the units [0, pair_units) from counter[0]; otherwise [pair_units,
 // total_units) from counter[1].  The two run as consecutive launches, so each
 // kernel holds one strip loop per dtype.
-template <bool kF32Log, bool kPair>
+template <bool kF32Log, bool kPair, bool kSd2>
 __global__ void __launch_bounds__(32 * kWarpsPerCta, 3) batch_kernel_fast(const unsigned char *table,
                                                                       unsigned long long *counter, int *status,
                                                                       const __grid_constant__ KParams kp8,
@@ -114,8 +114,10 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta, 3) batch_kernel_fast(const 
     const ImageView v = view_of(b);
     const long long local = u - b.unit_begin;
     const int64_t ux = local % b.units_x, uy = local / b.units_x;
-    if (b.elem == 1) fast_unit<uint8_t, kF32Log, kPair>(v, kp8, ux, uy, hdr->unit_w, hdr->unit_h, warp_words(words));
-    else fast_unit<uint16_t, kF32Log, kPair>(v, kp16, ux, uy, hdr->unit_w, hdr->unit_h, warp_words(words));
+    if (b.elem == 1)
+      fast_unit<uint8_t, kF32Log, kPair, kSd2>(v, kp8, ux, uy, hdr->unit_w, hdr->unit_h, warp_words(words));
+    else
+      fast_unit<uint16_t, kF32Log, kPair, kSd2>(v, kp16, ux, uy, hdr->unit_w, hdr->unit_h, warp_words(words));
   }
 }
 
@@ -148,12 +150,14 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta, 3) batch_kernel_redo(const 
 }
 
 // The streaming kernels of a plan's LoG mode.
+template <bool kF32Log, bool kPair>
+const void *fast_kernel_sd(const KParams &kp) {
+  return kp.sd_same ? reinterpret_cast<const void *>(&batch_kernel_fast<kF32Log, kPair, false>)
+                    : reinterpret_cast<const void *>(&batch_kernel_fast<kF32Log, kPair, true>);
+}
 const void *fast_kernel_of(const KParams &kp, bool pair) {
-  if (kp.f32log)
-    return pair ? reinterpret_cast<const void *>(&batch_kernel_fast<true, true>)
-                : reinterpret_cast<const void *>(&batch_kernel_fast<true, false>);
-  return pair ? reinterpret_cast<const void *>(&batch_kernel_fast<false, true>)
-              : reinterpret_cast<const void *>(&batch_kernel_fast<false, false>);
+  if (kp.f32log) return pair ? fast_kernel_sd<true, true>(kp) : fast_kernel_sd<true, false>(kp);
+  return pair ? fast_kernel_sd<false, true>(kp) : fast_kernel_sd<false, false>(kp);
 }
 const void *redo_kernel_of(const KParams &kp) {
   return kp.f32log ? reinterpret_cast<const void *>(&batch_kernel_redo<true>)

@@ -4,7 +4,7 @@
 namespace fx {
 namespace {
 
-template <typename T, bool kRedoPass, bool kF32Log, bool kPair>
+template <typename T, bool kRedoPass, bool kF32Log, bool kPair, bool kSd2>
 __global__ void __launch_bounds__(32 * kWarpsPerCta, 3) stream_kernel(const __grid_constant__ ImageView v,
                                                                   const __grid_constant__ KParams kp,
                                                                   int64_t units_x, int64_t units, int uh) {
@@ -14,7 +14,15 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta, 3) stream_kernel(const __gr
   if constexpr (kRedoPass)
     fast_unit_redo<T, kF32Log>(v, kp, unit % units_x, unit / units_x, kDefaultUnitW, uh, warp_words(words));
   else
-    fast_unit<T, kF32Log, kPair>(v, kp, unit % units_x, unit / units_x, kDefaultUnitW, uh, warp_words(words));
+    fast_unit<T, kF32Log, kPair, kSd2>(v, kp, unit % units_x, unit / units_x, kDefaultUnitW, uh,
+                                       warp_words(words));
+}
+
+template <typename T, bool kF32Log, bool kPair>
+void launch_first(const ImageView &v, const KParams &kp, cudaStream_t s, unsigned g, int64_t units_x,
+                  int64_t units, int uh) {
+  if (kp.sd_same) stream_kernel<T, false, kF32Log, kPair, false><<<g, 32 * kWarpsPerCta, 0, s>>>(v, kp, units_x, units, uh);
+  else stream_kernel<T, false, kF32Log, kPair, true><<<g, 32 * kWarpsPerCta, 0, s>>>(v, kp, units_x, units, uh);
 }
 
 template <typename T, bool kF32Log>
@@ -22,14 +30,12 @@ void launch_mode(const ImageView &v, const KParams &kp, cudaStream_t s, int64_t 
                  int64_t units, int uh) {
   const unsigned g = static_cast<unsigned>(blocks);
   if (kp.fbound >= 0) {
-    if (pair_loads_ok(v))
-      stream_kernel<T, false, kF32Log, true><<<g, 32 * kWarpsPerCta, 0, s>>>(v, kp, units_x, units, uh);
-    else
-      stream_kernel<T, false, kF32Log, false><<<g, 32 * kWarpsPerCta, 0, s>>>(v, kp, units_x, units, uh);
+    if (pair_loads_ok(v)) launch_first<T, kF32Log, true>(v, kp, s, g, units_x, units, uh);
+    else launch_first<T, kF32Log, false>(v, kp, s, g, units_x, units, uh);
   }
   // the second pass recomputes the strips the first one marked (all when fbound < 0)
   if (kp.fbound < 0 || kp.fbound < (sizeof(T) == 1 ? 255 : 65535))
-    stream_kernel<T, true, kF32Log, false><<<g, 32 * kWarpsPerCta, 0, s>>>(v, kp, units_x, units, uh);
+    stream_kernel<T, true, kF32Log, false, true><<<g, 32 * kWarpsPerCta, 0, s>>>(v, kp, units_x, units, uh);
 }
 
 template <typename T>

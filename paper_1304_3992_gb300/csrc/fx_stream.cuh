@@ -138,7 +138,6 @@ struct Ar<kModeF32> {
     const bool pass = d5 >= kp.ttmax[f] ? d3 >= kp.tt3[f] : d5 >= kp.tt5[f];
     return pass ? 0x80000000u : 0u;
   }
-  static __device__ __forceinline__ V fix(const KParams &kp, int f, V x) { return kp.fixzero[f] ? x + 0.0f : x; }
 };
 
 // Integer path: any uint16 value (|L| < 2^30 by the plan's range check).
@@ -164,7 +163,6 @@ struct Ar<kModeInt> {
     const bool pass = d5 > kp.tsdmax[f] ? d3 > kp.tsd3[f] : d5 > kp.tsd5[f];
     return pass ? 0x80000000u : 0u;
   }
-  static __device__ __forceinline__ V fix(const KParams &, int, V x) { return x; }
 };
 
 // FP32-LoG mode, values <= fbound (32-bit standard-deviation sums).  L is
@@ -198,7 +196,8 @@ struct Ar<kModeF32LogWide> : Ar<kModeF32> {
 // two single-pixel loads.  Either way every load is unconditional and lands in
 // a ring slot that is read four steps later, so loads overlap the arithmetic;
 // the clamped (replicated, reading R2) columns are selected when a row is used.
-template <typename T, int kMode, bool kPair>
+// kSd2: the branches have different standard-deviation thresholds (two S words).
+template <typename T, int kMode, bool kPair, bool kSd2>
 struct Strip {
   using A = Ar<kMode>;
   using V = typename A::V;
@@ -401,23 +400,24 @@ struct Strip {
         const float d8 = __fmaf_rn(-4.0f, R0, R8);
 #pragma unroll
         for (int f = 0; f < 2; ++f) {
-          float l = __fmul_rn(A::w(kp, f, 1), d1);
+          // starting from +0: a zero product gives +0, so no sum is ever -0
+          float l = __fmaf_rn(A::w(kp, f, 1), d1, 0.0f);
           l = __fmaf_rn(A::w(kp, f, 2), d2, l);
           l = __fmaf_rn(A::w(kp, f, 3), d4, l);
           l = __fmaf_rn(A::w(kp, f, 4), d5, l);
-          l = __fmaf_rn(A::w(kp, f, 5), d8, l);  // positive last weight: no -0 (else fix)
-          L_[f][c0][j] = A::fix(kp, f, l);
+          L_[f][c0][j] = __fmaf_rn(A::w(kp, f, 5), d8, l);
         }
       } else {
 #pragma unroll
         for (int f = 0; f < 2; ++f) {
-          V l = A::w(kp, f, 0) * R0;
+          // exact partial sums; starting from +0 no sum is ever -0 (the sign bit
+          // of L is the sign of the response)
+          V l = A::w(kp, f, 0) * R0 + V(0);
           l = l + A::w(kp, f, 1) * R1;
           l = l + A::w(kp, f, 2) * R2;
           l = l + A::w(kp, f, 3) * R4;
           l = l + A::w(kp, f, 4) * R5;
-          l = l + A::w(kp, f, 5) * R8;  // positive outer weight last: no -0 (else fix)
-          L_[f][c0][j] = A::fix(kp, f, l);
+          L_[f][c0][j] = l + A::w(kp, f, 5) * R8;
         }
       }
       const V A3 = R0 + R1 + R2;
@@ -425,7 +425,7 @@ struct Strip {
       const Q Q3 = c3_[m1][j] + c3_[c0][j] + c3_[p1][j];
       const Q Q5 = c5_[m2][j] + c5_[m1][j] + c5_[c0][j] + c5_[p1][j] + c5n[j];
       S_[0][c0][j] = A::sdpass(kp, 0, A3, A5, Q3, Q5);
-      if (!kp.sd_same) S_[1][c0][j] = A::sdpass(kp, 1, A3, A5, Q3, Q5);
+      if (kSd2) S_[1][c0][j] = A::sdpass(kp, 1, A3, A5, Q3, Q5);
     }
     // replicated borders for the L stage (reading R2)
     if (c >= Hrel) {
@@ -474,7 +474,7 @@ struct Strip {
     }
     put(acc_[10], S_[0][r][1]);
     put(acc_[10], S_[0][r][0]);
-    if (!kp.sd_same) {
+    if (kSd2) {
       put(acc_[11], S_[1][r][1]);
       put(acc_[11], S_[1][r][0]);
     }
@@ -502,7 +502,7 @@ struct Strip {
       const uint32_t lN = xN & ~(neg ^ sN), lS = xS & ~(neg ^ sS);
       const uint32_t znz = (xE | xW | xN | xS) & ~(lE | lW | lN | lS);
       const uint32_t z0 = ~(neg | pos) & ((nW & pE) | (pW & nE) | (nN & pS) | (pN & nS));
-      const uint32_t sd = kp.sd_same ? blk(10) : blk(10 + f);
+      const uint32_t sd = kSd2 ? blk(10 + f) : blk(10);
       m |= (znz | z0) & ~cf & sd;
     }
     // replicated borders for the mask (reading R2)
@@ -653,17 +653,18 @@ constexpr int kStripWords = 20;
 using StripWords = uint32_t[kWarpsPerCta][kStripWords][32];
 __device__ __forceinline__ uint32_t (*warp_words(StripWords &w))[32] { return w[(threadIdx.x >> 5) % kWarpsPerCta]; }
 
-// kF32Log selects the FP32-LoG mode (KParams::f32log) at compile time.
-template <typename T, bool kF32Log, bool kPair>
+// kF32Log selects the FP32-LoG mode (KParams::f32log) at compile time; kSd2 =
+// !KParams::sd_same (kSd2 = true is correct for any thresholds).
+template <typename T, bool kF32Log, bool kPair, bool kSd2>
 __device__ __forceinline__ void fast_unit(const ImageView &v, const KParams &kp, int64_t ux, int64_t uy, int,
                                           int uh, uint32_t (*words)[32]) {
   constexpr int kMode = kF32Log ? st::kModeF32Log : st::kModeF32;
-  static_assert(st::Strip<T, kMode, kPair>::kWords == kStripWords, "shared word layout");
+  static_assert(st::Strip<T, kMode, kPair, kSd2>::kWords == kStripWords, "shared word layout");
   if (kp.fbound < 0) return;
   const int64_t X0 = ux * st::kOutCols;
   const int64_t Y0 = v.y_begin + uy * uh;
   const int64_t Y1 = Y0 + uh < v.y_end ? Y0 + uh : v.y_end;
-  st::Strip<T, kMode, kPair> s(v, kp, X0, Y0, Y1, words);
+  st::Strip<T, kMode, kPair, kSd2> s(v, kp, X0, Y0, Y1, words);
   if (!s.run() && (threadIdx.x & 31) == 0) *unit_marker(v, ux, uy, uh) = kRedo;
 }
 
@@ -679,7 +680,7 @@ __device__ __forceinline__ void fast_unit_redo(const ImageView &v, const KParams
   const int64_t X0 = ux * st::kOutCols;
   const int64_t Y0 = v.y_begin + uy * uh;
   const int64_t Y1 = Y0 + uh < v.y_end ? Y0 + uh : v.y_end;
-  st::Strip<T, kMode, false> s(v, kp, X0, Y0, Y1, words);
+  st::Strip<T, kMode, false, true> s(v, kp, X0, Y0, Y1, words);
   s.run();
 }
 

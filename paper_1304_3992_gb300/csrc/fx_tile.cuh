@@ -97,12 +97,11 @@ __device__ __forceinline__ float log_f32(const KParams &kp, int f, const int32_t
   const float d1 = static_cast<float>(R[1] - 4 * R[0]), d2 = static_cast<float>(R[2] - 4 * R[0]);
   const float d4 = static_cast<float>(R[3] - 4 * R[0]), d5 = static_cast<float>(R[4] - 8 * R[0]);
   const float d8 = static_cast<float>(R[5] - 4 * R[0]);
-  float l = __fmul_rn(kp.ringf[f][1], d1);
+  float l = __fmaf_rn(kp.ringf[f][1], d1, 0.0f);  // from +0: never -0
   l = __fmaf_rn(kp.ringf[f][2], d2, l);
   l = __fmaf_rn(kp.ringf[f][3], d4, l);
   l = __fmaf_rn(kp.ringf[f][4], d5, l);
-  l = __fmaf_rn(kp.ringf[f][5], d8, l);
-  return kp.fixzero[f] ? __fadd_rn(l, 0.0f) : l;
+  return __fmaf_rn(kp.ringf[f][5], d8, l);
 }
 
 // Contrast test of Sec. 3.2 over the pixel and its 4 neighbours (clamped
