@@ -108,6 +108,9 @@ template <>
 struct Ar<kModeF32> {
   static constexpr bool kRel = false;     // L from the ring sums R_c directly
   static constexpr bool kChecked = true;  // values above fbound send the strip to the redo pass
+  // Eq. 2 sums of squares are taken over the biased bits K + u (K = 0x4B000000,
+  // the bits of the FP32 value u + 2^23) and the bias is removed in sdpass.
+  static constexpr bool kBiased = true;
   using V = float;
   using Q = uint32_t;
   static __device__ __forceinline__ V cvt(uint32_t u) { return __uint_as_float(0x4B000000u | u) - 8388608.0f; }
@@ -129,12 +132,17 @@ struct Ar<kModeF32> {
   static __device__ __forceinline__ uint32_t cfail(const KParams &kp, int f, V mx, V mn) {
     return __float_as_uint((mx - mn) - kp.tzc1f[f]);
   }
-  // sign bit set  <=>  the standard-deviation test passes (reading R4)
+  // sign bit set  <=>  the standard-deviation test passes (reading R4).
+  // Q = sum (K + u)^2 = sum u^2 + 2K A (mod 2^32, as K^2 = 0), so
+  // D = Lambda sum u^2 - A^2 = Lambda Q - b (b + c)  with b = K + A = bits(A + 2^23)
+  // and c = 16K (Lambda = 9) or 48K (Lambda = 25); -b - c is the bit pattern of
+  // one exact FFMA of A (2^-117 - A 2^-141, resp. A 2^-77 - 2^-53).  D < 2^32.
   static __device__ __forceinline__ uint32_t sdpass(const KParams &kp, int f, V A3, V A5, Q Q3, Q Q5) {
-    const uint32_t a3 = __float_as_uint(A3 + 8388608.0f) - 0x4B000000u;
-    const uint32_t a5 = __float_as_uint(A5 + 8388608.0f) - 0x4B000000u;
-    const uint32_t d3 = 9u * Q3 - a3 * a3;   // exact modulo 2^32, and D < 2^32
-    const uint32_t d5 = 25u * Q5 - a5 * a5;
+    const uint32_t b3 = __float_as_uint(A3 + 8388608.0f), b5 = __float_as_uint(A5 + 8388608.0f);
+    const uint32_t n3 = __float_as_uint(__fmaf_rn(A3, -0x1p-141f, 0x1p-117f));
+    const uint32_t n5 = __float_as_uint(__fmaf_rn(A5, 0x1p-77f, -0x1p-53f));
+    const uint32_t d3 = Q3 * 9u + b3 * n3;
+    const uint32_t d5 = Q5 * 25u + b5 * n5;
     const bool pass = d5 >= kp.ttmax[f] ? d3 >= kp.tt3[f] : d5 >= kp.tt5[f];
     return pass ? 0x80000000u : 0u;
   }
@@ -145,6 +153,7 @@ template <>
 struct Ar<kModeInt> {
   static constexpr bool kRel = false;
   static constexpr bool kChecked = false;
+  static constexpr bool kBiased = false;
   using V = int32_t;
   using Q = uint64_t;
   static __device__ __forceinline__ V cvt(uint32_t u) { return static_cast<int32_t>(u); }
@@ -178,6 +187,7 @@ template <>
 struct Ar<kModeF32LogWide> : Ar<kModeF32> {
   static constexpr bool kRel = true;
   static constexpr bool kChecked = false;
+  static constexpr bool kBiased = false;
   using Q = uint64_t;
   static __device__ __forceinline__ Q sq(uint32_t u) { return static_cast<uint64_t>(u) * u; }
   static __device__ __forceinline__ uint32_t sdpass(const KParams &kp, int f, V A3, V A5, Q Q3, Q Q5) {
@@ -297,9 +307,9 @@ struct Strip {
   // Row t (relative to Y0) into ring slot S.  Rows outside the image clamp to
   // it (reading R2); rows outside the buffer (a row band) clamp to the buffer:
   // they feed only rows that are not stored.
-  template <int S>
+  template <int S, bool kClamp = true>
   __device__ __forceinline__ void load_row(int32_t tr) {
-    const int32_t yr = tr < rlo ? rlo : (tr > rhi ? rhi : tr);
+    const int32_t yr = kClamp ? (tr < rlo ? rlo : (tr > rhi ? rhi : tr)) : tr;
     const uint64_t off = static_cast<uint64_t>(static_cast<uint32_t>(yr - rbase)) * pitch32;
     if constexpr (kPair) {
       if constexpr (sizeof(T) == 2) raw_[S] = __ldg(reinterpret_cast<const uint32_t *>(p0_ + off));
@@ -311,6 +321,8 @@ struct Strip {
   }
 
   // The lane's two pixels of the row in slot S as a 16-bit pair (column 0 low).
+  // (The selection also copies the ring slot before the next load refills it;
+  // reading the slot directly made that load wait on its predecessor's use.)
   template <int S>
   __device__ __forceinline__ uint32_t pixels() const {
     if constexpr (kPair) return __byte_perm(raw_[S], 0, sel_);
@@ -342,32 +354,51 @@ struct Strip {
     return m;
   }
 
-  template <int S>
+  // kChk: the step may need the border fix-ups of the L stage (a border strip,
+  // or rows next to the first or last image row); otherwise they are no-ops.
+  template <int S, bool kChk>
   __device__ __forceinline__ void step(int32_t t) {  // t relative to Y0, S = t & 3
     const uint32_t w = pixels<S>();
-    load_row<S>(t + 4);  // four rows ahead, into the slot just read
+    load_row<S, kChk>(t + 4);  // four rows ahead, into the slot just read
     if (check) vmax_ = __vmaxu2(vmax_, w);
     const uint32_t hl = __shfl_up_sync(kFull, w, 1);    // columns -2, -1
     const uint32_t hr = __shfl_down_sync(kFull, w, 1);  // columns 2, 3
-    const uint32_t u[6] = {hl & 0xFFFFu, hl >> 16, w & 0xFFFFu, w >> 16, hr & 0xFFFFu, hr >> 16};
     V fv[6];
-    Q sq[6];
+    Q c3n[2], c5n[2];
+    if constexpr (A::kBiased) {
+      // biased bits K + u of the six pixels (columns -2 .. 3); FP32 value = bits - 2^23
+      const uint32_t b[6] = {__byte_perm(hl, 0x4B000000u, 0x7610), __byte_perm(hl, 0x4B000000u, 0x7632),
+                             __byte_perm(w, 0x4B000000u, 0x7610), __byte_perm(w, 0x4B000000u, 0x7632),
+                             __byte_perm(hr, 0x4B000000u, 0x7610), __byte_perm(hr, 0x4B000000u, 0x7632)};
 #pragma unroll
-    for (int k = 0; k < 6; ++k) {
-      fv[k] = A::cvt(u[k]);
-      sq[k] = A::sq(u[k]);
+      for (int k = 0; k < 6; ++k) fv[k] = __uint_as_float(b[k]) - 8388608.0f;
+      const uint32_t s23 = b[2] * b[2] + b[3] * b[3];
+      c3n[0] = b[1] * b[1] + s23;
+      c3n[1] = b[4] * b[4] + s23;
+      c5n[0] = b[0] * b[0] + (b[4] * b[4] + c3n[0]);
+      c5n[1] = b[5] * b[5] + (b[1] * b[1] + c3n[1]);
+    } else {
+      const uint32_t u[6] = {hl & 0xFFFFu, hl >> 16, w & 0xFFFFu, w >> 16, hr & 0xFFFFu, hr >> 16};
+      Q sq[6];
+#pragma unroll
+      for (int k = 0; k < 6; ++k) {
+        fv[k] = A::cvt(u[k]);
+        sq[k] = A::sq(u[k]);
+      }
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        c3n[j] = sq[j + 1] + sq[j + 2] + sq[j + 3];
+        c5n[j] = c3n[j] + sq[j] + sq[j + 4];
+      }
     }
     V fn[2], h1n[2], h2n[2];
-    Q c3n[2], c5n[2];
 #pragma unroll
     for (int j = 0; j < 2; ++j) {
       fn[j] = fv[j + 2];
       h1n[j] = fv[j + 1] + fv[j + 3];
       h2n[j] = fv[j] + fv[j + 4];
-      c3n[j] = sq[j + 1] + sq[j + 2] + sq[j + 3];
-      c5n[j] = c3n[j] + sq[j] + sq[j + 4];
     }
-    centre<S>(t - 2, fn, h1n, h2n, c5n);
+    centre<S, kChk>(t - 2, fn, h1n, h2n, c5n);
 #pragma unroll
     for (int j = 0; j < 2; ++j) {
       f_[S][j] = fn[j];
@@ -381,7 +412,7 @@ struct Strip {
 
   // LoG responses and the standard-deviation test for the centre row c = t - 2
   // (row t arrives in fn / h1n / h2n / c5n; slot S still holds row t - 4).
-  template <int S>
+  template <int S, bool kChk>
   __device__ __forceinline__ void centre(int32_t c, const V fn[2], const V h1n[2], const V h2n[2],
                                          const Q c5n[2]) {
     constexpr int c0 = (S + 2) & 3, m1 = (S + 1) & 3, p1 = (S + 3) & 3, m2 = S;
@@ -428,21 +459,23 @@ struct Strip {
       if (kSd2) S_[1][c0][j] = A::sdpass(kp, 1, A3, A5, Q3, Q5);
     }
     // replicated borders for the L stage (reading R2)
-    if (c >= Hrel) {
+    if constexpr (kChk) {
+      if (c >= Hrel) {
 #pragma unroll
-      for (int f = 0; f < 2; ++f)
+        for (int f = 0; f < 2; ++f)
 #pragma unroll
-        for (int j = 0; j < 2; ++j) L_[f][c0][j] = L_[f][m1][j];
-    }
-    if (border) {
-      fix_cols(L_[0][c0]);
-      fix_cols(L_[1][c0]);
-    }
-    if (c == -Y0rel) {
+          for (int j = 0; j < 2; ++j) L_[f][c0][j] = L_[f][m1][j];
+      }
+      if (border) {
+        fix_cols(L_[0][c0]);
+        fix_cols(L_[1][c0]);
+      }
+      if (c == -Y0rel) {
 #pragma unroll
-      for (int f = 0; f < 2; ++f)
+        for (int f = 0; f < 2; ++f)
 #pragma unroll
-        for (int j = 0; j < 2; ++j) L_[f][m1][j] = L_[f][c0][j];
+          for (int j = 0; j < 2; ++j) L_[f][m1][j] = L_[f][c0][j];
+      }
     }
 #pragma unroll
     for (int f = 0; f < 2; ++f) {
@@ -603,11 +636,12 @@ struct Strip {
     return true;
   }
 
+  template <bool kChk>
   __device__ __forceinline__ void four_steps(int32_t t0) {  // t0 = 4k relative to Y0
-    step<0>(t0);
-    step<1>(t0 + 1);
-    step<2>(t0 + 2);
-    step<3>(t0 + 3);
+    step<0, kChk>(t0);
+    step<1, kChk>(t0 + 1);
+    step<2, kChk>(t0 + 2);
+    step<3, kChk>(t0 + 3);
   }
 
   __device__ bool run() {
@@ -622,7 +656,13 @@ struct Strip {
     const int32_t bmax = static_cast<int32_t>((Y1 - Y0 + 2) / 16);
     const int32_t iters = 4 * (bmax + 3);
     for (int32_t k = -2; k < iters; ++k) {
-      four_steps(4 * k);
+      // centre rows of this iteration: 4k - 2 .. 4k + 1 and loaded rows 4k + 4 ..
+      // 4k + 7 (relative to Y0); the fix-ups act only on a border strip, at image
+      // row 0 and past row H - 1, and loads clamp only outside [rlo, rhi]
+      const bool chk = border || (4 * k - 2 <= -Y0rel && -Y0rel <= 4 * k + 1) || 4 * k + 1 >= Hrel ||
+                       4 * k + 4 < rlo || 4 * k + 7 > rhi;
+      if (chk) four_steps<true>(4 * k);
+      else four_steps<false>(4 * k);
       if ((k & 3) == 3 && !end_group(k >> 2)) return false;
     }
     return true;
