@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-vs-plain comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-fp32", action="store_true", help="skip the FP32-LoG mode measurement")
+    ap.add_argument("--no-variants", action="store_true",
+                    help="skip the parameter variants (crossing-map source, median levels, grayscale median)")
     ap.add_argument("--side", type=int, default=SIDE, help="band side (default 16384)")
     ap.add_argument("--serve-duration", type=float, default=10.0,
                     help="seconds of the Poisson serving run (0 skips it; 60 is the full workload)")
@@ -297,6 +299,11 @@ def main():
     if not args.no_fp32:
         fp32 = bench_fp32_log(fx, torch, stream, bands, outs, max(3, args.warmup), min(K, 10))
 
+    # ---- parameter variants and the grayscale median op on band 0
+    variants = None
+    if not args.no_variants:
+        variants = bench_variants(fx, torch, stream, bands[0], outs[0])
+
     # ---- end to end through the C ABI on pinned host buffers
     h_in = [torch.from_numpy(b).pin_memory() for b in bands_np]
     h_out = [torch.empty(b.shape, dtype=torch.uint8).pin_memory() for b in bands_np]
@@ -367,7 +374,7 @@ def main():
             # per band: the streaming kernel and the integer redo check (12-bit data
             # is within the FP32-exact bound, so the redo kernel only reads markers)
             "gpu_launches": K * BANDS * 2, "clocks": clk, "batched": batched, "serving": serving,
-            "fp32_log": fp32,
+            "fp32_log": fp32, "variants": variants,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -402,6 +409,48 @@ def bench_fp32_log(fx, torch, stream, bands, outs_int, warmup, steps):
     return {"gpx_s": px * steps / (e0.elapsed_time(e1) * 1e-3) / 1e9, "kernel_ms": sum(ms) / len(ms),
             "steps": steps, "differs_from_integer_mode": diff / px,
             "launch": "fx_extract per band, log_mode FX_LOG_FP32 (FP32 pass + wide-pass marker check)"}
+
+
+def bench_variants(fx, torch, stream, band, out, reps=5):
+    """Throughput of fx_extract on one band for the parameter variants (which
+    kernel runs them is recorded), and of the grayscale hybrid median op."""
+    base = dict(sigma=(0.5, 20.0), mask_q=512)
+    cases = {
+        "median_off": (dict(hmf=()), "streaming"),
+        "median_3": (dict(hmf=(3,)), "streaming"),
+        "median_5_then_3": (dict(hmf=(5, 3)), "streaming"),
+        "median_5_then_5": (dict(hmf=(5, 5)), "general tile"),
+        "stddev_over_crossing_map": (dict(stddev_source=1, t_sd5=(0.2, 0.3), t_sdmax=(0.45, 0.5),
+                                          t_sd3=(0.3, 0.4)), "general tile"),
+    }
+    px = band.numel()
+    res = {}
+
+    def timed(fn):
+        for _ in range(2):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ms = []
+        for _ in range(reps):
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        return sorted(ms)[len(ms) // 2]
+
+    for name, (kw, kernel) in cases.items():
+        p = fx.make_params(fx.FX_U16, 12, **kw)
+        ms = timed(lambda: fx.extract(band, p, out=out, stream=stream))
+        res[name] = {"gpx_s": px / ms / 1e6, "ms": ms, "kernel": kernel}
+    med = torch.empty_like(band)
+    for w in (3, 5):
+        ms = timed(lambda: fx.hybrid_median(band, w, out=med, stream=stream))
+        res[f"grayscale_median_{w}"] = {"gpx_s": px / ms / 1e6, "ms": ms, "kernel": "median tile",
+                                        "gb_s": 4 * px / ms / 1e6}
+    res["workload"] = f"one {band.shape[0]}x{band.shape[1]} uint16 12-bit band, median of {reps} timed calls"
+    return res
 
 
 def bench_batched(fx, torch, dev, params, plan_cls):

@@ -48,9 +48,12 @@ cudaError_t launch_t(const ImageView &v, const KParams &kp, cudaStream_t s, int6
 
 }  // namespace
 
-// The streaming kernel covers the default configuration: image source for the
-// standard deviation and at most one median pass.
-bool fast_path_supported(const KParams &kp) { return kp.source == 0 && kp.nhmf <= 1; }
+// The streaming kernel covers the image source for the standard deviation and
+// up to two median passes whose radii add up to at most 3 (its 6-column halo:
+// 2 LoG + 1 crossing + 3 median).
+bool fast_path_supported(const KParams &kp) {
+  return kp.source == 0 && (kp.nhmf <= 1 || (kp.nhmf == 2 && kp.r_m <= 3));
+}
 
 // One aligned load per lane and row: base and pitch multiples of two pixels,
 // even width (so every lane's clamped columns lie in one aligned pair).

@@ -233,9 +233,11 @@ struct Strip {
   uint32_t acc_[12];
   // Words of earlier blocks, touched once per 16 rows, live in shared memory:
   // kBlk.. = previous block (12 words), kPneg / kPpos / kPsS = neg / pos / sS of
-  // the block before it, kMA / kMB = mask words of the two previous blocks.
+  // the block before it, kMA / kMB = mask words of the two previous blocks,
+  // kHA / kHB = first median level's words of the two blocks before (two levels).
   uint32_t (*sw_)[32];
-  static constexpr int kBlk = 0, kPneg = 12, kPpos = 14, kPsS = 16, kMA = 18, kMB = 19, kWords = 20;
+  static constexpr int kBlk = 0, kPneg = 12, kPpos = 14, kPsS = 16, kMA = 18, kMB = 19, kHA = 20, kHB = 21,
+                       kWords = 22;
   __device__ __forceinline__ uint32_t &blk(int i) { return sw_[kBlk + i][lane]; }
 
   // load state: rows relative to Y0; p0_ / p1_ address row rbase
@@ -538,7 +540,13 @@ struct Strip {
       const uint32_t sd = kSd2 ? blk(10 + f) : blk(10);
       m |= (znz | z0) & ~cf & sd;
     }
-    // replicated borders for the mask (reading R2)
+    return replicate(b, m, sw_[kMA][lane]);
+  }
+
+  // Replicated borders of a binary stage (reading R2) for block b: rows above
+  // row 0 / below row H - 1 and columns outside the image take the nearest
+  // image pixel's bit (prev: the stage's word of block b - 1).
+  __device__ __forceinline__ uint32_t replicate(int64_t b, uint32_t m, uint32_t prev) {
     const int64_t r0 = Y0 - 3 + 16 * b;  // image row of bit-row 0
     if (r0 < 0) {  // top: rows -3..-1 take row 0 (bit-row 3)
       const uint32_t pr = (m >> 24) & 0x3u;
@@ -551,35 +559,34 @@ struct Strip {
         const uint32_t pr = (m >> (30 - 2 * rH)) & 0x3u;
         m = (m & keep) | ((pr * 0x55555555u) & ~keep);
       } else {
-        m = (sw_[kMA][lane] & 0x3u) * 0x55555555u;
+        m = (prev & 0x3u) * 0x55555555u;
       }
     }
     if (border) m = fix_cols_bits(m);
     return m;
   }
 
-  // Hybrid median of block own (prev / next: the blocks above / below) and
-  // the store of its output rows.
-  __device__ __forceinline__ void median_store(int64_t b, uint32_t prev, uint32_t own, uint32_t next) {
-    uint32_t h = own;
-    const int k = kp.nhmf ? kp.hmf[0] : 0;
-    if (k) {
-      const uint32_t oP = __shfl_up_sync(kFull, own, 1), oX = __shfl_down_sync(kFull, own, 1);
-      const uint32_t pP = __shfl_up_sync(kFull, prev, 1), pX = __shfl_down_sync(kFull, prev, 1);
-      const uint32_t xP = __shfl_up_sync(kFull, next, 1), xX = __shfl_down_sync(kFull, next, 1);
-      const uint32_t E1o = e1(own, oX), W1o = w1(own, oP), E1p = e1(prev, pX), W1p = w1(prev, pP);
-      const uint32_t E1n = e1(next, xX), W1n = w1(next, xP);
-      if (k == 5) {  // two columns over: the neighbour lane's word itself
-        const uint32_t plus[9] = {own, E1o, W1o, oX, oP, n1(own, prev), s1(own, next), n2(own, prev), s2(own, next)};
-        const uint32_t cross[9] = {own, n1(E1o, E1p), n1(W1o, W1p), s1(E1o, E1n), s1(W1o, W1n),
-                                   n2(oX, pX), n2(oP, pP), s2(oX, xX), s2(oP, xP)};
-        h = maj3(maj9(plus), maj9(cross), own);
-      } else {
-        const uint32_t plus[5] = {own, E1o, W1o, n1(own, prev), s1(own, next)};
-        const uint32_t cross[5] = {own, n1(E1o, E1p), n1(W1o, W1p), s1(E1o, E1n), s1(W1o, W1n)};
-        h = maj3(maj5(plus), maj5(cross), own);
-      }
+  // Hybrid median with window k (3 or 5) of block own (prev / next: the blocks
+  // above / below).
+  __device__ __forceinline__ uint32_t median(uint32_t prev, uint32_t own, uint32_t next, int k) {
+    const uint32_t oP = __shfl_up_sync(kFull, own, 1), oX = __shfl_down_sync(kFull, own, 1);
+    const uint32_t pP = __shfl_up_sync(kFull, prev, 1), pX = __shfl_down_sync(kFull, prev, 1);
+    const uint32_t xP = __shfl_up_sync(kFull, next, 1), xX = __shfl_down_sync(kFull, next, 1);
+    const uint32_t E1o = e1(own, oX), W1o = w1(own, oP), E1p = e1(prev, pX), W1p = w1(prev, pP);
+    const uint32_t E1n = e1(next, xX), W1n = w1(next, xP);
+    if (k == 5) {  // two columns over: the neighbour lane's word itself
+      const uint32_t plus[9] = {own, E1o, W1o, oX, oP, n1(own, prev), s1(own, next), n2(own, prev), s2(own, next)};
+      const uint32_t cross[9] = {own, n1(E1o, E1p), n1(W1o, W1p), s1(E1o, E1n), s1(W1o, W1n),
+                                 n2(oX, pX), n2(oP, pP), s2(oX, xX), s2(oP, xP)};
+      return maj3(maj9(plus), maj9(cross), own);
     }
+    const uint32_t plus[5] = {own, E1o, W1o, n1(own, prev), s1(own, next)};
+    const uint32_t cross[5] = {own, n1(E1o, E1p), n1(W1o, W1p), s1(E1o, E1n), s1(W1o, W1n)};
+    return maj3(maj5(plus), maj5(cross), own);
+  }
+
+  // Store of the output rows of block b (mask words h).
+  __device__ __forceinline__ void store(int64_t b, uint32_t h) {
     const int64_t x = xs + 2 * lane;
     const bool lane_out = lane >= 3 && lane < 29 && x < W;
     if (!lane_out) return;
@@ -622,7 +629,15 @@ struct Strip {
     }
     uint32_t m = 0;
     if (g >= 1) m = mask_block(g - 1);
-    if (g >= 2) median_store(g - 2, sw_[kMB][lane], sw_[kMA][lane], m);
+    if (kp.nhmf < 2) {
+      if (g >= 2) store(g - 2, kp.nhmf ? median(sw_[kMB][lane], sw_[kMA][lane], m, kp.hmf[0]) : sw_[kMA][lane]);
+    } else {  // two median levels: the first one's words are a stage of their own
+      uint32_t h1 = 0;
+      if (g >= 2) h1 = replicate(g - 2, median(sw_[kMB][lane], sw_[kMA][lane], m, kp.hmf[0]), sw_[kHA][lane]);
+      if (g >= 3) store(g - 3, median(sw_[kHB][lane], sw_[kHA][lane], h1, kp.hmf[1]));
+      sw_[kHB][lane] = sw_[kHA][lane];
+      sw_[kHA][lane] = h1;
+    }
     sw_[kMB][lane] = sw_[kMA][lane];
     sw_[kMA][lane] = m;
 #pragma unroll
@@ -654,7 +669,7 @@ struct Strip {
     load_row<2>(-6);
     load_row<3>(-5);
     const int32_t bmax = static_cast<int32_t>((Y1 - Y0 + 2) / 16);
-    const int32_t iters = 4 * (bmax + 3);
+    const int32_t iters = 4 * (bmax + (kp.nhmf < 2 ? 3 : 4));  // one more block of delay per extra level
     for (int32_t k = -2; k < iters; ++k) {
       // centre rows of this iteration: 4k - 2 .. 4k + 1 and loaded rows 4k + 4 ..
       // 4k + 7 (relative to Y0); the fix-ups act only on a border strip, at image
@@ -689,7 +704,7 @@ __device__ __forceinline__ uint8_t *unit_marker(const ImageView &v, int64_t ux, 
 
 // Per-warp shared words of the streaming path (the caller's kernel owns one
 // array of this type per CTA and passes the warp's slice).
-constexpr int kStripWords = 20;
+constexpr int kStripWords = 22;
 using StripWords = uint32_t[kWarpsPerCta][kStripWords][32];
 __device__ __forceinline__ uint32_t (*warp_words(StripWords &w))[32] { return w[(threadIdx.x >> 5) % kWarpsPerCta]; }
 

@@ -244,3 +244,27 @@ def test_device_pointer_checks(cuda_lib):
     assert lib.fx_extract(img.data_ptr(), 8, 8, 16, fx.FX_U16, ctypes.byref(q), out.data_ptr(), None) == 3
     nanp = fx.make_params(fx.FX_U16, t_zc=(float("nan"), 0.0))
     assert lib.fx_extract(img.data_ptr(), 8, 8, 16, fx.FX_U16, ctypes.byref(nanp), out.data_ptr(), None) == 1
+
+
+@pytest.mark.parametrize("hmf", [(5, 3), (3, 5), (3, 3)])
+def test_two_level_median_streaming(cuda_lib, hmf):
+    """Two median levels with radii adding up to 3 run on the streaming kernel
+    (Sec. 4.2's repeated passes); full masks of images taller than one work
+    unit, both dtypes, against the oracle, and the batched plan against
+    single calls."""
+    imgs = [scenes.scene(700, 1100, seed=61, n_rects=300, noise_sigma=24.0, impulse_frac=0.01, bits=12),
+            scenes.scene(1030, 613, seed=62, n_rects=250, noise_sigma=4.0, impulse_frac=0.01, bits=8)]
+    d, p = pair(16.0, hmf=hmf)
+    singles = []
+    for img in imgs:
+        dd = dict(d) if img.dtype == np.uint16 else dict(oracle.default_params(1.0), hmf=hmf)
+        pp = p if img.dtype == np.uint16 else cuda_lib.params_from_dict(dd)
+        got = run(cuda_lib, img, pp)
+        assert_same(got, oracle.extract(img, dd), f"hmf {hmf} {img.dtype}")
+        singles.append((img, pp, got))
+    img, pp, ref = singles[0]
+    pairs = [(dev(img), torch.zeros(img.shape, dtype=torch.uint8, device="cuda"))]
+    with cuda_lib.Plan(pp, max_images=2) as plan:
+        plan.extract_batch(pairs)
+        torch.cuda.synchronize()
+        assert_same(pairs[0][1].cpu().numpy(), ref, f"batched hmf {hmf}")
