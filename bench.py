@@ -421,7 +421,7 @@ def bench_variants(fx, torch, stream, band, out, reps=5):
         "median_5_then_3": (dict(hmf=(5, 3)), "streaming"),
         "median_5_then_5": (dict(hmf=(5, 5)), "general tile"),
         "stddev_over_crossing_map": (dict(stddev_source=1, t_sd5=(0.2, 0.3), t_sdmax=(0.45, 0.5),
-                                          t_sd3=(0.3, 0.4)), "general tile"),
+                                          t_sd3=(0.3, 0.4)), "streaming"),
     }
     px = band.numel()
     res = {}

@@ -196,13 +196,14 @@ fx_status fx_extract_batch(fx_plan *plan, const fx_image_desc *descs, int32_t n,
 /*
  * Work-unit shape of the batched kernel and its CTAs per SM.  A unit is a
  * strip of tile_w output columns by tile_h output rows walked by one warp;
- * tile_w must be 52 (the strip width of the streaming kernel) and tile_h a
- * multiple of 16 in [16, 8192]; ctas_per_sm is in 1..8 (4 warps per CTA).
- * fx_plan_autotune times the candidate shapes {52 x 256, 512, 1024, 2048} x
- * every CTAs-per-SM count the kernel's occupancy allows on the given images
- * (their outputs are overwritten) and keeps the fastest; fx_plan_set_tile
- * forces one.  Plans whose parameters need the general kernel (stddev over
- * the crossing map, or more than one median level) use its fixed 64 x 32
+ * tile_w must be the strip width of the streaming kernel (52, or 48 when the
+ * standard deviation is taken over the crossing map) and tile_h a multiple
+ * of 16 in [16, 8192]; ctas_per_sm is in 1..8 (4 warps per CTA).
+ * fx_plan_autotune times the heights {256, 512, 1024, 2048} x every
+ * CTAs-per-SM count the kernel's occupancy allows on the given images (their
+ * outputs are overwritten) and keeps the fastest; fx_plan_set_tile forces
+ * one.  Plans whose parameters need the general kernel (median windows whose
+ * radii add up to more than 3, or more than two levels) use its fixed 64 x 32
  * tile; for them only ctas_per_sm takes effect.
  * Errors: FX_ERR_INVALID_ARG (shape or count out of range), FX_ERR_CUDA.
  */

@@ -149,6 +149,24 @@ fx_status make_kparams(const fx_params *p, int32_t maxval, KParams *kp) {
     kp->tt3[f] = tt(kp->tsd3[f]);
   }
   kp->sd_same = kp->tsd5[0] == kp->tsd5[1] && kp->tsdmax[0] == kp->tsdmax[1] && kp->tsd3[0] == kp->tsd3[1];
+  // crossing-map source: the counts n in [0, Lambda] with n (Lambda - n) > t form
+  // an interval (the product is concave in n); encode its bounds bit by bit
+  auto interval = [](int64_t t, int lambda, int bits, uint32_t *sel) {
+    int lo = (1 << bits) - 1, hi = 0;
+    for (int n = lambda; n >= 0; --n)
+      if (static_cast<int64_t>(n) * (lambda - n) > t) lo = n;
+    for (int n = 0; n <= lambda; ++n)
+      if (static_cast<int64_t>(n) * (lambda - n) > t) hi = n;
+    for (int i = 0; i < bits; ++i) {
+      sel[i] = (lo >> i) & 1 ? 0xFFFFFFFFu : 0u;
+      sel[bits + i] = (hi >> i) & 1 ? 0xFFFFFFFFu : 0u;
+    }
+  };
+  for (int f = 0; f < 2; ++f) {
+    interval(kp->tsd5[f], 25, 5, kp->zsel[f]);
+    interval(kp->tsdmax[f], 25, 5, kp->zsel[f] + 10);
+    interval(kp->tsd3[f], 9, 4, kp->zsel[f] + 20);
+  }
   return FX_OK;
 }
 

@@ -41,6 +41,13 @@ struct KParams {
   // test is fl(max - min) > tzf (t_zc rounded down to FP32).
   int32_t f32log;
   float tzf[2];
+  // Crossing-map source (source 1): with n crossings in a window of Lambda
+  // pixels D = n (Lambda - n), so each test D > t holds for n in an interval.
+  // Per branch, bit masks (all ones / zero) of the interval bounds, LSB first:
+  // [0..4] lo and [5..9] hi of the 5x5 test, [10..19] of the 5x5 test against
+  // t_sdmax, [20..23] lo and [24..27] hi of the 3x3 test.  An empty interval
+  // has lo above every count.
+  uint32_t zsel[2][28];
 };
 
 // Derive KParams from fx_params for images whose values are <= maxval.

@@ -90,7 +90,7 @@ __global__ void __launch_bounds__(256) batch_kernel_general(const unsigned char 
 // kPair: the units [0, pair_units) from counter[0]; otherwise [pair_units,
 // total_units) from counter[1].  The two run as consecutive launches, so each
 // kernel holds one strip loop per dtype.
-template <bool kF32Log, bool kPair, bool kSd2>
+template <bool kF32Log, bool kPair, bool kSd2, bool kSrcZ>
 __global__ void __launch_bounds__(32 * kWarpsPerCta, 3) batch_kernel_fast(const unsigned char *table,
                                                                       unsigned long long *counter, int *status,
                                                                       const __grid_constant__ KParams kp8,
@@ -115,16 +115,16 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta, 3) batch_kernel_fast(const 
     const long long local = u - b.unit_begin;
     const int64_t ux = local % b.units_x, uy = local / b.units_x;
     if (b.elem == 1)
-      fast_unit<uint8_t, kF32Log, kPair, kSd2>(v, kp8, ux, uy, hdr->unit_w, hdr->unit_h, warp_words(words));
+      fast_unit<uint8_t, kF32Log, kPair, kSd2, kSrcZ>(v, kp8, ux, uy, hdr->unit_w, hdr->unit_h, warp_words(words));
     else
-      fast_unit<uint16_t, kF32Log, kPair, kSd2>(v, kp16, ux, uy, hdr->unit_w, hdr->unit_h, warp_words(words));
+      fast_unit<uint16_t, kF32Log, kPair, kSd2, kSrcZ>(v, kp16, ux, uy, hdr->unit_w, hdr->unit_h, warp_words(words));
   }
 }
 
 // Second pass of the streaming path: every warp walks the units with a static
 // stride and recomputes, on the integer (or wide FP32-LoG) path, the strips
 // the first pass marked.
-template <bool kF32Log>
+template <bool kF32Log, bool kSrcZ>
 __global__ void __launch_bounds__(32 * kWarpsPerCta, 3) batch_kernel_redo(const unsigned char *table,
                                                                       unsigned long long *, int *,
                                                                       const __grid_constant__ KParams kp8,
@@ -142,26 +142,32 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta, 3) batch_kernel_redo(const 
     const int64_t ux = local % b.units_x, uy = local / b.units_x;
     if (b.elem == 1) {
       if (kp8.fbound < 0 || kp8.fbound < 255)
-        fast_unit_redo<uint8_t, kF32Log>(v, kp8, ux, uy, hdr->unit_w, hdr->unit_h, warp_words(words));
+        fast_unit_redo<uint8_t, kF32Log, kSrcZ>(v, kp8, ux, uy, hdr->unit_w, hdr->unit_h, warp_words(words));
     } else {
-      fast_unit_redo<uint16_t, kF32Log>(v, kp16, ux, uy, hdr->unit_w, hdr->unit_h, warp_words(words));
+      fast_unit_redo<uint16_t, kF32Log, kSrcZ>(v, kp16, ux, uy, hdr->unit_w, hdr->unit_h, warp_words(words));
     }
   }
 }
 
-// The streaming kernels of a plan's LoG mode.
+// The streaming kernels of a plan's parameters (LoG mode, load path,
+// standard-deviation source and thresholds).
 template <bool kF32Log, bool kPair>
 const void *fast_kernel_sd(const KParams &kp) {
-  return kp.sd_same ? reinterpret_cast<const void *>(&batch_kernel_fast<kF32Log, kPair, false>)
-                    : reinterpret_cast<const void *>(&batch_kernel_fast<kF32Log, kPair, true>);
+  if (kp.source == 1) return reinterpret_cast<const void *>(&batch_kernel_fast<kF32Log, kPair, false, true>);
+  return kp.sd_same ? reinterpret_cast<const void *>(&batch_kernel_fast<kF32Log, kPair, false, false>)
+                    : reinterpret_cast<const void *>(&batch_kernel_fast<kF32Log, kPair, true, false>);
 }
 const void *fast_kernel_of(const KParams &kp, bool pair) {
   if (kp.f32log) return pair ? fast_kernel_sd<true, true>(kp) : fast_kernel_sd<true, false>(kp);
   return pair ? fast_kernel_sd<false, true>(kp) : fast_kernel_sd<false, false>(kp);
 }
+template <bool kF32Log>
+const void *redo_kernel_src(const KParams &kp) {
+  return kp.source == 1 ? reinterpret_cast<const void *>(&batch_kernel_redo<kF32Log, true>)
+                        : reinterpret_cast<const void *>(&batch_kernel_redo<kF32Log, false>);
+}
 const void *redo_kernel_of(const KParams &kp) {
-  return kp.f32log ? reinterpret_cast<const void *>(&batch_kernel_redo<true>)
-                   : reinterpret_cast<const void *>(&batch_kernel_redo<false>);
+  return kp.f32log ? redo_kernel_src<true>(kp) : redo_kernel_src<false>(kp);
 }
 
 }  // namespace
@@ -278,7 +284,7 @@ fx_status fill_table(fx_plan *p, unsigned char *h, const fx_image_desc *d, int32
   BatchHeader *hdr = reinterpret_cast<BatchHeader *>(h);
   BatchImage *ims = reinterpret_cast<BatchImage *>(h + sizeof(BatchHeader));
   const int uw = p->fast ? p->unit_w : gen::TW, uh = p->fast ? p->unit_h : gen::TH;
-  const int uwx = p->fast ? kDefaultUnitW : gen::TW;  // output columns per unit
+  const int uwx = p->fast ? strip_width(p->kp8.source == 1) : gen::TW;  // output columns per unit
   int64_t total = 0, pair_units = 0;
   // On the streaming path the queue runs through the images in four groups:
   // one aligned load per lane (uint16, then uint8), then pixel by pixel (uint16,
@@ -367,7 +373,7 @@ fx_status fx_plan_create(fx_plan **out, const fx_params *params, int32_t max_ima
   p->fast = fast_path_supported(p->kp8) && fast_path_supported(p->kp16);
   p->device = device;
   p->max_images = max_images;
-  p->unit_w = kDefaultUnitW;
+  p->unit_w = strip_width(p->kp8.source == 1);
   p->unit_h = kDefaultUnitH;
   p->ctas_per_sm = 2;
   if (cudaSetDevice(device) != cudaSuccess || cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
@@ -441,7 +447,7 @@ fx_status fx_extract_batch(fx_plan *p, const fx_image_desc *descs, int32_t n, vo
 
 fx_status fx_plan_set_tile(fx_plan *p, int32_t tile_w, int32_t tile_h, int32_t ctas_per_sm) {
   if (!p || ctas_per_sm < 1 || ctas_per_sm > 8) return FX_ERR_INVALID_ARG;
-  if (!fast_unit_shape_ok(tile_w, tile_h)) return FX_ERR_INVALID_ARG;
+  if (!fast_unit_shape_ok(tile_w, tile_h, p->kp8.source == 1)) return FX_ERR_INVALID_ARG;
   if (cudaSetDevice(p->device) != cudaSuccess) return FX_ERR_CUDA;
   for (int i = 0; i < 2; ++i)
     if (cudaEventSynchronize(p->h_free[i]) != cudaSuccess) return FX_ERR_CUDA;
@@ -461,9 +467,9 @@ fx_status fx_plan_autotune(fx_plan *p, const fx_image_desc *descs, int32_t n, vo
   int bw = p->unit_w, bh = p->unit_h, bc = p->ctas_per_sm;
   fx_status st = FX_OK;
   for (int c = 0; c < kNumUnitShapes && st == FX_OK; ++c) {
-    const int uw = kUnitShapes[c][0], uh = kUnitShapes[c][1];
+    const int uw = strip_width(p->kp8.source == 1), uh = kUnitShapes[c][1];
     for (int cps = 1; cps <= kMaxCtasPerSm && st == FX_OK; ++cps) {
-      if (!p->fast && (uw != kDefaultUnitW || uh != kDefaultUnitH)) continue;
+      if (!p->fast && uh != kDefaultUnitH) continue;
       if ((st = fx_plan_set_tile(p, uw, uh, cps)) != FX_OK) break;
       int occ = 0;
       if (p->fast) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fast_kernel_of(p->kp8, true), 32 * kWarpsPerCta, 0);

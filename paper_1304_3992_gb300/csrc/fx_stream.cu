@@ -4,7 +4,7 @@
 namespace fx {
 namespace {
 
-template <typename T, bool kRedoPass, bool kF32Log, bool kPair, bool kSd2>
+template <typename T, bool kRedoPass, bool kF32Log, bool kPair, bool kSd2, bool kSrcZ>
 __global__ void __launch_bounds__(32 * kWarpsPerCta, 3) stream_kernel(const __grid_constant__ ImageView v,
                                                                   const __grid_constant__ KParams kp,
                                                                   int64_t units_x, int64_t units, int uh) {
@@ -12,30 +12,34 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta, 3) stream_kernel(const __gr
   const int64_t unit = static_cast<int64_t>(blockIdx.x) * kWarpsPerCta + (threadIdx.x >> 5);
   if (unit >= units) return;  // whole warps only
   if constexpr (kRedoPass)
-    fast_unit_redo<T, kF32Log>(v, kp, unit % units_x, unit / units_x, kDefaultUnitW, uh, warp_words(words));
+    fast_unit_redo<T, kF32Log, kSrcZ>(v, kp, unit % units_x, unit / units_x, 0, uh, warp_words(words));
   else
-    fast_unit<T, kF32Log, kPair, kSd2>(v, kp, unit % units_x, unit / units_x, kDefaultUnitW, uh,
-                                       warp_words(words));
+    fast_unit<T, kF32Log, kPair, kSd2, kSrcZ>(v, kp, unit % units_x, unit / units_x, 0, uh, warp_words(words));
 }
 
 template <typename T, bool kF32Log, bool kPair>
 void launch_first(const ImageView &v, const KParams &kp, cudaStream_t s, unsigned g, int64_t units_x,
                   int64_t units, int uh) {
-  if (kp.sd_same) stream_kernel<T, false, kF32Log, kPair, false><<<g, 32 * kWarpsPerCta, 0, s>>>(v, kp, units_x, units, uh);
-  else stream_kernel<T, false, kF32Log, kPair, true><<<g, 32 * kWarpsPerCta, 0, s>>>(v, kp, units_x, units, uh);
+  constexpr int nt = 32 * kWarpsPerCta;
+  if (kp.source == 1) stream_kernel<T, false, kF32Log, kPair, false, true><<<g, nt, 0, s>>>(v, kp, units_x, units, uh);
+  else if (kp.sd_same) stream_kernel<T, false, kF32Log, kPair, false, false><<<g, nt, 0, s>>>(v, kp, units_x, units, uh);
+  else stream_kernel<T, false, kF32Log, kPair, true, false><<<g, nt, 0, s>>>(v, kp, units_x, units, uh);
 }
 
 template <typename T, bool kF32Log>
 void launch_mode(const ImageView &v, const KParams &kp, cudaStream_t s, int64_t blocks, int64_t units_x,
                  int64_t units, int uh) {
   const unsigned g = static_cast<unsigned>(blocks);
+  constexpr int nt = 32 * kWarpsPerCta;
   if (kp.fbound >= 0) {
     if (pair_loads_ok(v)) launch_first<T, kF32Log, true>(v, kp, s, g, units_x, units, uh);
     else launch_first<T, kF32Log, false>(v, kp, s, g, units_x, units, uh);
   }
   // the second pass recomputes the strips the first one marked (all when fbound < 0)
-  if (kp.fbound < 0 || kp.fbound < (sizeof(T) == 1 ? 255 : 65535))
-    stream_kernel<T, true, kF32Log, false, true><<<g, 32 * kWarpsPerCta, 0, s>>>(v, kp, units_x, units, uh);
+  if (kp.fbound < 0 || kp.fbound < (sizeof(T) == 1 ? 255 : 65535)) {
+    if (kp.source == 1) stream_kernel<T, true, kF32Log, false, true, true><<<g, nt, 0, s>>>(v, kp, units_x, units, uh);
+    else stream_kernel<T, true, kF32Log, false, true, false><<<g, nt, 0, s>>>(v, kp, units_x, units, uh);
+  }
 }
 
 template <typename T>
@@ -48,12 +52,10 @@ cudaError_t launch_t(const ImageView &v, const KParams &kp, cudaStream_t s, int6
 
 }  // namespace
 
-// The streaming kernel covers the image source for the standard deviation and
-// up to two median passes whose radii add up to at most 3 (its 6-column halo:
-// 2 LoG + 1 crossing + 3 median).
-bool fast_path_supported(const KParams &kp) {
-  return kp.source == 0 && (kp.nhmf <= 1 || (kp.nhmf == 2 && kp.r_m <= 3));
-}
+// The streaming kernel covers both standard-deviation sources and up to two
+// median passes whose radii add up to at most 3 (its halo: 2 LoG + 1 crossing
+// (+ 2 crossing-map deviation) + 3 median columns).
+bool fast_path_supported(const KParams &kp) { return kp.nhmf <= 1 || (kp.nhmf == 2 && kp.r_m <= 3); }
 
 // One aligned load per lane and row: base and pitch multiples of two pixels,
 // even width (so every lane's clamped columns lie in one aligned pair).
@@ -64,7 +66,8 @@ bool pair_loads_ok(const ImageView &v) {
 
 cudaError_t launch_fast(const ImageView &v, const KParams &kp, cudaStream_t s) {
   const int uh = kDefaultUnitH;
-  const int64_t units_x = (v.width + kDefaultUnitW - 1) / kDefaultUnitW;
+  const int uw = strip_width(kp.source == 1);
+  const int64_t units_x = (v.width + uw - 1) / uw;
   const int64_t units_y = (v.y_end - v.y_begin + uh - 1) / uh;
   const int64_t units = units_x * units_y;
   if (units <= 0) return cudaSuccess;

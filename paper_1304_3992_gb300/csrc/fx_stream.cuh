@@ -40,20 +40,23 @@
 namespace fx {
 
 constexpr int kDefaultUnitW = 52;
+// Output columns of a strip: 52, or 48 when the standard deviation is taken
+// over the crossing map (its 5x5 window adds 2 columns to the halo).
+constexpr int strip_width(bool src_z) { return src_z ? 48 : 52; }
 constexpr int kDefaultUnitH = 512;
 constexpr int kNumUnitShapes = 4;
 constexpr int kUnitShapes[kNumUnitShapes][2] = {{52, 256}, {52, 512}, {52, 1024}, {52, 2048}};
 constexpr int kMaxCtasPerSm = 8;
 constexpr int kWarpsPerCta = 4;
 
-inline bool fast_unit_shape_ok(int w, int h) { return w == 52 && h >= 16 && h <= 8192 && h % 16 == 0; }
+inline bool fast_unit_shape_ok(int w, int h, bool src_z) {
+  return w == strip_width(src_z) && h >= 16 && h <= 8192 && h % 16 == 0;
+}
 inline size_t fast_smem_bytes(int, int, int) { return 0; }
 
 namespace st {
 
 constexpr unsigned kFull = 0xffffffffu;
-constexpr int kLeftHalo = 6;
-constexpr int kOutCols = 52;
 constexpr int kWinCols = 64;
 constexpr uint32_t M0 = 0x55555555u, M1 = 0xAAAAAAAAu;  // bits of column 0 / column 1
 
@@ -72,6 +75,15 @@ __device__ __forceinline__ void fadd(uint32_t a, uint32_t b, uint32_t c, uint32_
   k = (a & b) | (c & (a ^ b));
 }
 __device__ __forceinline__ uint32_t maj3(uint32_t a, uint32_t b, uint32_t c) { return (a & b) | (c & (a | b)); }
+// bitwise count of five bits: n = c0 + 2 c1 + 4 c2
+__device__ __forceinline__ void count5(uint32_t a, uint32_t b, uint32_t c, uint32_t d, uint32_t e, uint32_t &c0,
+                                       uint32_t &c1, uint32_t &c2) {
+  uint32_t s1, k1, k2;
+  fadd(a, b, c, s1, k1);
+  fadd(d, e, s1, c0, k2);
+  c1 = k1 ^ k2;
+  c2 = k1 & k2;
+}
 // bitwise "at least 5 of 9"
 __device__ __forceinline__ uint32_t maj9(const uint32_t x[9]) {
   uint32_t s1, c1, s2, c2, s3, c3, s4, c4;
@@ -207,9 +219,14 @@ struct Ar<kModeF32LogWide> : Ar<kModeF32> {
 // a ring slot that is read four steps later, so loads overlap the arithmetic;
 // the clamped (replicated, reading R2) columns are selected when a row is used.
 // kSd2: the branches have different standard-deviation thresholds (two S words).
-template <typename T, int kMode, bool kPair, bool kSd2>
+// kSrcZ: the standard deviation is taken over each branch's crossing map
+// (reading R4, source 1) from bit-sliced counts, at block level.
+template <typename T, int kMode, bool kPair, bool kSd2, bool kSrcZ>
 struct Strip {
   using A = Ar<kMode>;
+  // halo columns left of the strip (even: the pair loads are aligned) and
+  // output columns: 2 LoG + 1 crossing (+ 2 standard deviation) + up to 3 median
+  static constexpr int kLeftHalo = kSrcZ ? 8 : 6, kOutCols = strip_width(kSrcZ);
   using V = typename A::V;
   using Q = typename A::Q;
 
@@ -234,10 +251,12 @@ struct Strip {
   // Words of earlier blocks, touched once per 16 rows, live in shared memory:
   // kBlk.. = previous block (12 words), kPneg / kPpos / kPsS = neg / pos / sS of
   // the block before it, kMA / kMB = mask words of the two previous blocks,
-  // kHA / kHB = first median level's words of the two blocks before (two levels).
+  // kHA / kHB = first median level's words of the two blocks before (two levels),
+  // kZA / kZB = crossing words of the two blocks before and kPcf = contrast words
+  // of the block before (kSrcZ).
   uint32_t (*sw_)[32];
   static constexpr int kBlk = 0, kPneg = 12, kPpos = 14, kPsS = 16, kMA = 18, kMB = 19, kHA = 20, kHB = 21,
-                       kWords = 22;
+                       kZA = 22, kZB = 24, kPcf = 26, kWords = 28;
   __device__ __forceinline__ uint32_t &blk(int i) { return sw_[kBlk + i][lane]; }
 
   // load state: rows relative to Y0; p0_ / p1_ address row rbase
@@ -366,7 +385,7 @@ struct Strip {
     const uint32_t hl = __shfl_up_sync(kFull, w, 1);    // columns -2, -1
     const uint32_t hr = __shfl_down_sync(kFull, w, 1);  // columns 2, 3
     V fv[6];
-    Q c3n[2], c5n[2];
+    Q c3n[2] = {}, c5n[2] = {};
     if constexpr (A::kBiased) {
       // biased bits K + u of the six pixels (columns -2 .. 3); FP32 value = bits - 2^23
       const uint32_t b[6] = {__byte_perm(hl, 0x4B000000u, 0x7610), __byte_perm(hl, 0x4B000000u, 0x7632),
@@ -374,11 +393,13 @@ struct Strip {
                              __byte_perm(hr, 0x4B000000u, 0x7610), __byte_perm(hr, 0x4B000000u, 0x7632)};
 #pragma unroll
       for (int k = 0; k < 6; ++k) fv[k] = __uint_as_float(b[k]) - 8388608.0f;
-      const uint32_t s23 = b[2] * b[2] + b[3] * b[3];
-      c3n[0] = b[1] * b[1] + s23;
-      c3n[1] = b[4] * b[4] + s23;
-      c5n[0] = b[0] * b[0] + (b[4] * b[4] + c3n[0]);
-      c5n[1] = b[5] * b[5] + (b[1] * b[1] + c3n[1]);
+      if constexpr (!kSrcZ) {
+        const uint32_t s23 = b[2] * b[2] + b[3] * b[3];
+        c3n[0] = b[1] * b[1] + s23;
+        c3n[1] = b[4] * b[4] + s23;
+        c5n[0] = b[0] * b[0] + (b[4] * b[4] + c3n[0]);
+        c5n[1] = b[5] * b[5] + (b[1] * b[1] + c3n[1]);
+      }
     } else {
       const uint32_t u[6] = {hl & 0xFFFFu, hl >> 16, w & 0xFFFFu, w >> 16, hr & 0xFFFFu, hr >> 16};
       Q sq[6];
@@ -387,10 +408,12 @@ struct Strip {
         fv[k] = A::cvt(u[k]);
         sq[k] = A::sq(u[k]);
       }
+      if constexpr (!kSrcZ) {
 #pragma unroll
-      for (int j = 0; j < 2; ++j) {
-        c3n[j] = sq[j + 1] + sq[j + 2] + sq[j + 3];
-        c5n[j] = c3n[j] + sq[j] + sq[j + 4];
+        for (int j = 0; j < 2; ++j) {
+          c3n[j] = sq[j + 1] + sq[j + 2] + sq[j + 3];
+          c5n[j] = c3n[j] + sq[j] + sq[j + 4];
+        }
       }
     }
     V fn[2], h1n[2], h2n[2];
@@ -453,12 +476,14 @@ struct Strip {
           L_[f][c0][j] = l + A::w(kp, f, 5) * R8;
         }
       }
-      const V A3 = R0 + R1 + R2;
-      const V A5 = A3 + R4 + R5 + R8;
-      const Q Q3 = c3_[m1][j] + c3_[c0][j] + c3_[p1][j];
-      const Q Q5 = c5_[m2][j] + c5_[m1][j] + c5_[c0][j] + c5_[p1][j] + c5n[j];
-      S_[0][c0][j] = A::sdpass(kp, 0, A3, A5, Q3, Q5);
-      if (kSd2) S_[1][c0][j] = A::sdpass(kp, 1, A3, A5, Q3, Q5);
+      if constexpr (!kSrcZ) {
+        const V A3 = R0 + R1 + R2;
+        const V A5 = A3 + R4 + R5 + R8;
+        const Q Q3 = c3_[m1][j] + c3_[c0][j] + c3_[p1][j];
+        const Q Q5 = c5_[m2][j] + c5_[m1][j] + c5_[c0][j] + c5_[p1][j] + c5n[j];
+        S_[0][c0][j] = A::sdpass(kp, 0, A3, A5, Q3, Q5);
+        if (kSd2) S_[1][c0][j] = A::sdpass(kp, 1, A3, A5, Q3, Q5);
+      }
     }
     // replicated borders for the L stage (reading R2)
     if constexpr (kChk) {
@@ -507,6 +532,7 @@ struct Strip {
         put(acc_[5 * f + 4], A::cfail(kp, f, mx, mn));
       }
     }
+    if constexpr (kSrcZ) return;
     put(acc_[10], S_[0][r][1]);
     put(acc_[10], S_[0][r][0]);
     if (kSd2) {
@@ -515,32 +541,95 @@ struct Strip {
     }
   }
 
-  // Block b = g - 1 (words blk): zero crossings, extraction, OR (the mask M).
+  // Zero crossings (Sec. 3.2, reading R3) of branch f in block g - 1 (words blk;
+  // the row below from acc_, the row above from the kP* words).
+  __device__ __forceinline__ uint32_t crossings(int f) {
+    const uint32_t neg = blk(5 * f), pos = blk(5 * f + 1), sE = blk(5 * f + 2), sS = blk(5 * f + 3);
+    const uint32_t negP = __shfl_up_sync(kFull, neg, 1), negX = __shfl_down_sync(kFull, neg, 1);
+    const uint32_t posP = __shfl_up_sync(kFull, pos, 1), posX = __shfl_down_sync(kFull, pos, 1);
+    const uint32_t sEP = __shfl_up_sync(kFull, sE, 1);
+    const uint32_t nE = e1(neg, negX), pE = e1(pos, posX), nW = w1(neg, negP), pW = w1(pos, posP);
+    const uint32_t nN = n1(neg, sw_[kPneg + f][lane]), pN = n1(pos, sw_[kPpos + f][lane]);
+    const uint32_t nS = s1(neg, acc_[5 * f]), pS = s1(pos, acc_[5 * f + 1]);
+    const uint32_t sW = w1(sE, sEP), sN = n1(sS, sw_[kPsS + f][lane]);
+    // crossing with each neighbour, and losing it: the pixel wins an edge iff
+    // it is the negative one XOR the edge sum is negative (reading R3)
+    const uint32_t xE = (neg & pE) | (pos & nE), xW = (neg & pW) | (pos & nW);
+    const uint32_t xN = (neg & pN) | (pos & nN), xS = (neg & pS) | (pos & nS);
+    const uint32_t lE = xE & ~(neg ^ sE), lW = xW & ~(neg ^ sW);
+    const uint32_t lN = xN & ~(neg ^ sN), lS = xS & ~(neg ^ sS);
+    const uint32_t znz = (xE | xW | xN | xS) & ~(lE | lW | lN | lS);
+    const uint32_t z0 = ~(neg | pos) & ((nW & pE) | (pW & nE) | (nN & pS) | (pN & nS));
+    return znz | z0;
+  }
+
+  // Block b = g - 1 (image-source standard deviation): extraction and OR (the mask M).
   __device__ __forceinline__ uint32_t mask_block(int64_t b) {
     uint32_t m = 0;
 #pragma unroll
     for (int f = 0; f < 2; ++f) {
-      const uint32_t neg = blk(5 * f), pos = blk(5 * f + 1), sE = blk(5 * f + 2), sS = blk(5 * f + 3);
-      const uint32_t cf = blk(5 * f + 4);
-      const uint32_t negP = __shfl_up_sync(kFull, neg, 1), negX = __shfl_down_sync(kFull, neg, 1);
-      const uint32_t posP = __shfl_up_sync(kFull, pos, 1), posX = __shfl_down_sync(kFull, pos, 1);
-      const uint32_t sEP = __shfl_up_sync(kFull, sE, 1);
-      const uint32_t nE = e1(neg, negX), pE = e1(pos, posX), nW = w1(neg, negP), pW = w1(pos, posP);
-      const uint32_t nN = n1(neg, sw_[kPneg + f][lane]), pN = n1(pos, sw_[kPpos + f][lane]);
-      const uint32_t nS = s1(neg, acc_[5 * f]), pS = s1(pos, acc_[5 * f + 1]);
-      const uint32_t sW = w1(sE, sEP), sN = n1(sS, sw_[kPsS + f][lane]);
-      // crossing with each neighbour, and losing it: the pixel wins an edge iff
-      // it is the negative one XOR the edge sum is negative (reading R3)
-      const uint32_t xE = (neg & pE) | (pos & nE), xW = (neg & pW) | (pos & nW);
-      const uint32_t xN = (neg & pN) | (pos & nN), xS = (neg & pS) | (pos & nS);
-      const uint32_t lE = xE & ~(neg ^ sE), lW = xW & ~(neg ^ sW);
-      const uint32_t lN = xN & ~(neg ^ sN), lS = xS & ~(neg ^ sS);
-      const uint32_t znz = (xE | xW | xN | xS) & ~(lE | lW | lN | lS);
-      const uint32_t z0 = ~(neg | pos) & ((nW & pE) | (pW & nE) | (nN & pS) | (pN & nS));
       const uint32_t sd = kSd2 ? blk(10 + f) : blk(10);
-      m |= (znz | z0) & ~cf & sd;
+      m |= crossings(f) & ~blk(5 * f + 4) & sd;
     }
     return replicate(b, m, sw_[kMA][lane]);
+  }
+
+  // Bit-sliced n >= lo and n <= hi for the NB-bit counts n (planes n[0] = LSB);
+  // sel[i] / sel[NB + i] = all ones where bit i of lo / hi is set.
+  template <int NB>
+  __device__ __forceinline__ static uint32_t in_range(const uint32_t (&n)[NB], const uint32_t *sel) {
+    uint32_t ge = 0xFFFFFFFFu, le = 0xFFFFFFFFu;
+#pragma unroll
+    for (int i = 0; i < NB; ++i) {
+      ge = (sel[i] & n[i] & ge) | (~sel[i] & (n[i] | ge));
+      le = (sel[NB + i] & (~n[i] | le)) | (~sel[NB + i] & ~n[i] & le);
+    }
+    return ge & le;
+  }
+
+  // Eq. 2 over the binary crossing map of branch f (reading R4, source 1) for
+  // block own (prev / next: the blocks above / below).  With n crossings in a
+  // window of Lambda pixels, D = n (Lambda - n); each test D > t holds on an
+  // interval of n, precomputed on the host (KParams::zsel).
+  __device__ __forceinline__ uint32_t sd_over_z(uint32_t prev, uint32_t own, uint32_t next, int f) {
+    // vertical 3- and 5-row sums: t = (t1 t0), v = (v2 v1 v0)
+    const uint32_t a = n1(own, prev), c = s1(own, next), d = n2(own, prev), e = s2(own, next);
+    uint32_t t0, t1, v0, k1;
+    fadd(a, own, c, t0, t1);
+    fadd(t0, d, e, v0, k1);
+    const uint32_t v1 = t1 ^ k1, v2 = t1 & k1;
+    // the same sums of the neighbour lanes (two columns over) and one column over
+    const uint32_t t0P = __shfl_up_sync(kFull, t0, 1), t0X = __shfl_down_sync(kFull, t0, 1);
+    const uint32_t t1P = __shfl_up_sync(kFull, t1, 1), t1X = __shfl_down_sync(kFull, t1, 1);
+    const uint32_t v0P = __shfl_up_sync(kFull, v0, 1), v0X = __shfl_down_sync(kFull, v0, 1);
+    const uint32_t v1P = __shfl_up_sync(kFull, v1, 1), v1X = __shfl_down_sync(kFull, v1, 1);
+    const uint32_t v2P = __shfl_up_sync(kFull, v2, 1), v2X = __shfl_down_sync(kFull, v2, 1);
+    // 3x3 count: t(x-1) + t(x) + t(x+1), 4 bits
+    uint32_t x0, x1, y0, y1;
+    fadd(w1(t0, t0P), t0, e1(t0, t0X), x0, x1);
+    fadd(w1(t1, t1P), t1, e1(t1, t1X), y0, y1);
+    const uint32_t cc = x1 & y0;
+    const uint32_t n3[4] = {x0, x1 ^ y0, y1 ^ cc, y1 & cc};
+    // 5x5 count: v(x-2) + ... + v(x+2), 5 bits; each plane's five bits counted first
+    uint32_t p0, p1, p2, q0, q1, q2, r0, r1, r2;
+    count5(v0P, w1(v0, v0P), v0, e1(v0, v0X), v0X, p0, p1, p2);
+    count5(v1P, w1(v1, v1P), v1, e1(v1, v1X), v1X, q0, q1, q2);
+    count5(v2P, w1(v2, v2P), v2, e1(v2, v2X), v2X, r0, r1, r2);
+    // total = p0 + 2 (p1 + q0) + 4 (p2 + q1 + r0) + 8 (q2 + r1) + 16 r2
+    const uint32_t h1 = p1 ^ q0, hc = p1 & q0;
+    uint32_t s4, k4, g4, m4;
+    fadd(p2, q1, r0, s4, k4);     // weight 4 (carry k4 to 8)
+    const uint32_t t4 = s4 ^ hc;  // with the weight-2 carry
+    g4 = s4 & hc;                 // carry to 8
+    uint32_t s8, k8;
+    fadd(q2, r1, k4, s8, k8);     // weight 8 (carry k8 to 16)
+    const uint32_t u8 = s8 ^ g4;
+    m4 = s8 & g4;                 // carry to 16
+    const uint32_t n5[5] = {p0, h1, t4, u8, r2 ^ k8 ^ m4};  // the count is at most 25
+    const uint32_t *sel = kp.zsel[f];
+    const uint32_t p5 = in_range(n5, sel), pm = in_range(n5, sel + 10);
+    const uint32_t p3 = in_range(n3, sel + 20);
+    return (pm & p3) | (~pm & p5);
   }
 
   // Replicated borders of a binary stage (reading R2) for block b: rows above
@@ -588,7 +677,7 @@ struct Strip {
   // Store of the output rows of block b (mask words h).
   __device__ __forceinline__ void store(int64_t b, uint32_t h) {
     const int64_t x = xs + 2 * lane;
-    const bool lane_out = lane >= 3 && lane < 29 && x < W;
+    const bool lane_out = lane >= kLeftHalo / 2 && lane < (kLeftHalo + kOutCols) / 2 && x < W;
     if (!lane_out) return;
     const int64_t ybase = Y0 - 3 + 16 * b;
     // rows [ybase + rlo, ybase + rhi) of this block belong to the unit
@@ -628,13 +717,39 @@ struct Strip {
       if (__any_sync(kFull, m > static_cast<uint32_t>(kp.fbound))) return false;
     }
     uint32_t m = 0;
-    if (g >= 1) m = mask_block(g - 1);
+    int64_t gm;  // block index of m (the mask M)
+    if constexpr (kSrcZ) {
+      // crossings of block g - 1 (a replicated stage), then the standard
+      // deviation over them, extraction and OR for block g - 2
+      gm = g - 2;
+      uint32_t z[2] = {0, 0};
+#pragma unroll
+      for (int f = 0; f < 2; ++f)
+        if (g >= 0) z[f] = replicate(g - 1, crossings(f), sw_[kZA + f][lane]);
+      if (g >= 2) {
+#pragma unroll
+        for (int f = 0; f < 2; ++f) {
+          const uint32_t za = sw_[kZA + f][lane];
+          m |= za & ~sw_[kPcf + f][lane] & sd_over_z(sw_[kZB + f][lane], za, z[f], f);
+        }
+        m = replicate(gm, m, sw_[kMA][lane]);
+      }
+#pragma unroll
+      for (int f = 0; f < 2; ++f) {
+        sw_[kZB + f][lane] = sw_[kZA + f][lane];
+        sw_[kZA + f][lane] = z[f];
+        sw_[kPcf + f][lane] = blk(5 * f + 4);
+      }
+    } else {
+      gm = g - 1;
+      if (g >= 1) m = mask_block(g - 1);
+    }
     if (kp.nhmf < 2) {
-      if (g >= 2) store(g - 2, kp.nhmf ? median(sw_[kMB][lane], sw_[kMA][lane], m, kp.hmf[0]) : sw_[kMA][lane]);
+      if (gm >= 1) store(gm - 1, kp.nhmf ? median(sw_[kMB][lane], sw_[kMA][lane], m, kp.hmf[0]) : sw_[kMA][lane]);
     } else {  // two median levels: the first one's words are a stage of their own
       uint32_t h1 = 0;
-      if (g >= 2) h1 = replicate(g - 2, median(sw_[kMB][lane], sw_[kMA][lane], m, kp.hmf[0]), sw_[kHA][lane]);
-      if (g >= 3) store(g - 3, median(sw_[kHB][lane], sw_[kHA][lane], h1, kp.hmf[1]));
+      if (gm >= 1) h1 = replicate(gm - 1, median(sw_[kMB][lane], sw_[kMA][lane], m, kp.hmf[0]), sw_[kHA][lane]);
+      if (gm >= 2) store(gm - 2, median(sw_[kHB][lane], sw_[kHA][lane], h1, kp.hmf[1]));
       sw_[kHB][lane] = sw_[kHA][lane];
       sw_[kHA][lane] = h1;
     }
@@ -669,7 +784,8 @@ struct Strip {
     load_row<2>(-6);
     load_row<3>(-5);
     const int32_t bmax = static_cast<int32_t>((Y1 - Y0 + 2) / 16);
-    const int32_t iters = 4 * (bmax + (kp.nhmf < 2 ? 3 : 4));  // one more block of delay per extra level
+    // one more block of delay per extra median level and for the crossing-map source
+    const int32_t iters = 4 * (bmax + (kp.nhmf < 2 ? 3 : 4) + (kSrcZ ? 1 : 0));
     for (int32_t k = -2; k < iters; ++k) {
       // centre rows of this iteration: 4k - 2 .. 4k + 1 and loaded rows 4k + 4 ..
       // 4k + 7 (relative to Y0); the fix-ups act only on a border strip, at image
@@ -698,44 +814,46 @@ struct Strip {
 // register allocation of the FP32 one.
 constexpr uint8_t kRedo = 0xFF;
 
-__device__ __forceinline__ uint8_t *unit_marker(const ImageView &v, int64_t ux, int64_t uy, int uh) {
-  return v.out + (uy * uh) * v.out_pitch + ux * st::kOutCols;
+__device__ __forceinline__ uint8_t *unit_marker(const ImageView &v, int64_t ux, int64_t uy, int uh, int uw) {
+  return v.out + (uy * uh) * v.out_pitch + ux * uw;
 }
 
 // Per-warp shared words of the streaming path (the caller's kernel owns one
 // array of this type per CTA and passes the warp's slice).
-constexpr int kStripWords = 22;
+constexpr int kStripWords = 28;
 using StripWords = uint32_t[kWarpsPerCta][kStripWords][32];
 __device__ __forceinline__ uint32_t (*warp_words(StripWords &w))[32] { return w[(threadIdx.x >> 5) % kWarpsPerCta]; }
 
 // kF32Log selects the FP32-LoG mode (KParams::f32log) at compile time; kSd2 =
-// !KParams::sd_same (kSd2 = true is correct for any thresholds).
-template <typename T, bool kF32Log, bool kPair, bool kSd2>
+// !KParams::sd_same (kSd2 = true is correct for any thresholds); kSrcZ =
+// (KParams::source == 1).
+template <typename T, bool kF32Log, bool kPair, bool kSd2, bool kSrcZ>
 __device__ __forceinline__ void fast_unit(const ImageView &v, const KParams &kp, int64_t ux, int64_t uy, int,
                                           int uh, uint32_t (*words)[32]) {
   constexpr int kMode = kF32Log ? st::kModeF32Log : st::kModeF32;
-  static_assert(st::Strip<T, kMode, kPair, kSd2>::kWords == kStripWords, "shared word layout");
+  static_assert(st::Strip<T, kMode, kPair, kSd2, kSrcZ>::kWords == kStripWords, "shared word layout");
   if (kp.fbound < 0) return;
-  const int64_t X0 = ux * st::kOutCols;
+  constexpr int uw = strip_width(kSrcZ);
+  const int64_t X0 = ux * uw;
   const int64_t Y0 = v.y_begin + uy * uh;
   const int64_t Y1 = Y0 + uh < v.y_end ? Y0 + uh : v.y_end;
-  st::Strip<T, kMode, kPair, kSd2> s(v, kp, X0, Y0, Y1, words);
-  if (!s.run() && (threadIdx.x & 31) == 0) *unit_marker(v, ux, uy, uh) = kRedo;
+  st::Strip<T, kMode, kPair, kSd2, kSrcZ> s(v, kp, X0, Y0, Y1, words);
+  if (!s.run() && (threadIdx.x & 31) == 0) *unit_marker(v, ux, uy, uh, uw) = kRedo;
 }
 
-template <typename T, bool kF32Log>
+template <typename T, bool kF32Log, bool kSrcZ>
 __device__ __forceinline__ void fast_unit_redo(const ImageView &v, const KParams &kp, int64_t ux, int64_t uy,
                                                int, int uh, uint32_t (*words)[32]) {
   constexpr int kMode = kF32Log ? st::kModeF32LogWide : st::kModeInt;
   if (kp.fbound >= 0) {
     uint8_t mark = 0;
-    if ((threadIdx.x & 31) == 0) mark = *unit_marker(v, ux, uy, uh);
+    if ((threadIdx.x & 31) == 0) mark = *unit_marker(v, ux, uy, uh, strip_width(kSrcZ));
     if (__shfl_sync(st::kFull, mark, 0) != kRedo) return;
   }
-  const int64_t X0 = ux * st::kOutCols;
+  const int64_t X0 = ux * strip_width(kSrcZ);
   const int64_t Y0 = v.y_begin + uy * uh;
   const int64_t Y1 = Y0 + uh < v.y_end ? Y0 + uh : v.y_end;
-  st::Strip<T, kMode, false, true> s(v, kp, X0, Y0, Y1, words);
+  st::Strip<T, kMode, false, true, kSrcZ> s(v, kp, X0, Y0, Y1, words);
   s.run();
 }
 
