@@ -268,3 +268,28 @@ def test_two_level_median_streaming(cuda_lib, hmf):
         plan.extract_batch(pairs)
         torch.cuda.synchronize()
         assert_same(pairs[0][1].cpu().numpy(), ref, f"batched hmf {hmf}")
+
+
+@pytest.mark.parametrize("hmf", [(5,), (5, 3), (3,), ()])
+def test_crossing_map_source_streaming(cuda_lib, hmf):
+    """Standard deviation over the crossing map (reading R4, source 1) on the
+    streaming kernel (48-column strips, bit-sliced window counts): full masks of
+    images taller than one work unit, both dtypes, against the oracle, and the
+    batched plan against single calls."""
+    kw = dict(stddev_source=1, t_sd5=(0.2, 0.3), t_sdmax=(0.45, 0.5), t_sd3=(0.3, 0.4), hmf=hmf)
+    imgs = [scenes.scene(701, 1090, seed=71, n_rects=300, noise_sigma=24.0, impulse_frac=0.01, bits=12),
+            scenes.scene(1030, 613, seed=72, n_rects=250, noise_sigma=4.0, impulse_frac=0.01, bits=8)]
+    outs = []
+    for img in imgs:
+        scale = 16.0 if img.dtype == np.uint16 else 1.0
+        d, p = pair(scale, **kw)
+        got = run(cuda_lib, img, p)
+        assert got.sum() > 0
+        assert_same(got, oracle.extract(img, d), f"hmf {hmf} {img.dtype}")
+        outs.append((img, p, got))
+    img, p, ref = outs[0]
+    pairs = [(dev(img), torch.zeros(img.shape, dtype=torch.uint8, device="cuda"))]
+    with cuda_lib.Plan(p, max_images=2) as plan:
+        plan.extract_batch(pairs)
+        torch.cuda.synchronize()
+        assert_same(pairs[0][1].cpu().numpy(), ref, f"batched hmf {hmf}")
