@@ -154,9 +154,9 @@ def kernel_source_sha() -> str:
     return h.hexdigest()
 
 
-def profiled_traffic(kernel_key: str):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken on
-    the current kernel sources (else None)."""
+def profiled(kernel_key: str, field: str):
+    """A numeric field of the committed ncu summary, if it was taken on the
+    current kernel sources (else None)."""
     path = os.path.join(ROOT, "profiles", f"{kernel_key}.txt")
     if not os.path.exists(path):
         return None
@@ -168,9 +168,14 @@ def profiled_traffic(kernel_key: str):
     if kv.get("source_sha256") != kernel_source_sha():
         return None
     try:
-        return float(kv["dram_bytes_per_launch_full_size"])
-    except (KeyError, ValueError):
+        return float(kv[field].split()[0])
+    except (KeyError, ValueError, IndexError):
         return None
+
+
+def profiled_traffic(kernel_key: str):
+    """DRAM bytes per launch from the committed ncu summary (None if stale)."""
+    return profiled(kernel_key, "dram_bytes_per_launch_full_size")
 
 
 def peaks():
@@ -348,9 +353,14 @@ def main():
     clk = clocks.summary()
     mhz = clk["sm_mhz"] or 1900.0
     issue_peak = props.multi_processor_count * 128 * mhz * 1e6  # lane-instructions/s
+    px_per_s = px_launch / (avg_launch_ms * 1e-3)
     issue = {"sm_count": props.multi_processor_count, "sm_mhz": mhz,
              "peak_lane_inst_per_s": issue_peak,
-             "lane_inst_per_px_at_roof": issue_peak / (px_launch / (avg_launch_ms * 1e-3))}
+             "lane_inst_per_px_at_roof": issue_peak / px_per_s}
+    ipp = profiled("fused_extract_16384_u16", "lane_inst_per_px")
+    if ipp is not None:  # lane-instructions per pixel from the committed ncu summary
+        issue.update({"lane_inst_per_px": ipp, "achieved_lane_inst_per_s": px_per_s * ipp,
+                      "frac": px_per_s * ipp / issue_peak})
 
     cpu = None
     if rank == 0 and not args.no_cpu:

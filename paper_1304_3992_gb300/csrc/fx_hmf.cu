@@ -9,64 +9,163 @@
 //   med5           = med3(c, max(min(a, b), min(d, e)), min(max(a, b), max(d, e)))
 //   med9 of three triples = med3(max of the triples' minima,
 //                                med3 of their medians, min of their maxima)
-// One CTA stages its tile plus a 2-pixel halo in shared memory once.
+//
+// One warp walks down a strip of 60 output columns (a 64-column window with
+// one halo lane on each side), one input row per step.  Lane l holds the two
+// pixels of window columns 2l, 2l+1 as one u16x2 word, so every min/max
+// handles two pixels.  A ring of k rows keeps, per row, the words of the
+// lane's pixels shifted by -2..2 columns (neighbour lanes by shuffle, one-
+// column shifts by byte selection); loads are issued k rows ahead into a ring
+// of their own and never sit inside a branch.
 #include <cstdint>
+#include <utility>
 
 #include "fx_internal.h"
 
 namespace fx {
 namespace {
 
-constexpr int HW = 64, HH = 16, HR = 2, HNT = 256;
-constexpr int SW = HW + 2 * HR, SH = HH + 2 * HR;
+constexpr int kHmfOut = 60;    // output columns per strip (lanes 1..30)
+constexpr int kHmfUnitH = 256; // output rows per strip unit
+constexpr int kHmfWarps = 4;   // warps per CTA
+constexpr unsigned kAll = 0xffffffffu;
 
-__device__ __forceinline__ int mn(int a, int b) { return a < b ? a : b; }
-__device__ __forceinline__ int mx(int a, int b) { return a > b ? a : b; }
-__device__ __forceinline__ int med3(int a, int b, int c) { return mx(mn(a, b), mn(mx(a, b), c)); }
-__device__ __forceinline__ int med5(int a, int b, int c, int d, int e) {
-  return med3(c, mx(mn(a, b), mn(d, e)), mn(mx(a, b), mx(d, e)));
+__device__ __forceinline__ uint32_t vmin(uint32_t a, uint32_t b) {
+  uint32_t d;
+  asm("min.u16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+  return d;
+}
+__device__ __forceinline__ uint32_t vmax(uint32_t a, uint32_t b) {
+  uint32_t d;
+  asm("max.u16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+  return d;
+}
+__device__ __forceinline__ uint32_t med3(uint32_t a, uint32_t b, uint32_t c) {
+  return vmax(vmin(a, b), vmin(vmax(a, b), c));
+}
+__device__ __forceinline__ uint32_t med5(uint32_t a, uint32_t b, uint32_t c, uint32_t d, uint32_t e) {
+  return med3(c, vmax(vmin(a, b), vmin(d, e)), vmin(vmax(a, b), vmax(d, e)));
+}
+// minimum, median and maximum of a triple
+__device__ __forceinline__ void sort3(uint32_t a, uint32_t b, uint32_t c, uint32_t &lo, uint32_t &md,
+                                      uint32_t &hi) {
+  const uint32_t mn = vmin(a, b), mx = vmax(a, b);
+  lo = vmin(mn, c);
+  hi = vmax(mx, c);
+  md = vmax(mn, vmin(mx, c));
 }
 // median of {a0..a2} U {b0..b2} U {c0..c2}
-__device__ __forceinline__ int med9(int a0, int a1, int a2, int b0, int b1, int b2, int c0, int c1, int c2) {
-  const int alo = mn(mn(a0, a1), a2), ahi = mx(mx(a0, a1), a2), amd = a0 + a1 + a2 - alo - ahi;
-  const int blo = mn(mn(b0, b1), b2), bhi = mx(mx(b0, b1), b2), bmd = b0 + b1 + b2 - blo - bhi;
-  const int clo = mn(mn(c0, c1), c2), chi = mx(mx(c0, c1), c2), cmd = c0 + c1 + c2 - clo - chi;
-  return med3(mx(mx(alo, blo), clo), med3(amd, bmd, cmd), mn(mn(ahi, bhi), chi));
+__device__ __forceinline__ uint32_t med9(uint32_t a0, uint32_t a1, uint32_t a2, uint32_t b0, uint32_t b1,
+                                         uint32_t b2, uint32_t c0, uint32_t c1, uint32_t c2) {
+  uint32_t al, am, ah, bl, bm, bh, cl, cm, ch;
+  sort3(a0, a1, a2, al, am, ah);
+  sort3(b0, b1, b2, bl, bm, bh);
+  sort3(c0, c1, c2, cl, cm, ch);
+  return med3(vmax(vmax(al, bl), cl), med3(am, bm, cm), vmin(vmin(ah, bh), ch));
+}
+
+template <typename T, int K>
+struct HmfStrip {
+  static constexpr int R = K / 2;
+  const unsigned char *p0_, *p1_;  // this lane's two clamped columns in image row 0
+  int64_t pitch, H, Y0, Y1, W, x;
+  unsigned char *out_;
+  int64_t opitch;
+  int lane;
+  uint32_t raw0_[K], raw1_[K];  // loaded pixels of the next K rows
+  uint32_t win_[K][5];          // per ring row: the pair words shifted by -2..2 columns
+
+  __device__ HmfStrip(const T *img, int64_t W_, int64_t H_, int64_t pitch_, T *out, int64_t opitch_, int64_t X0,
+                      int64_t Y0_, int64_t Y1_)
+      : pitch(pitch_), H(H_), Y0(Y0_), Y1(Y1_), W(W_), out_(reinterpret_cast<unsigned char *>(out)),
+        opitch(opitch_) {
+    lane = threadIdx.x & 31;
+    x = X0 - 2 + 2 * lane;
+    const int64_t c0 = x < 0 ? 0 : (x >= W ? W - 1 : x), c1 = x + 1 < 0 ? 0 : (x + 1 >= W ? W - 1 : x + 1);
+    p0_ = reinterpret_cast<const unsigned char *>(img) + c0 * static_cast<int64_t>(sizeof(T));
+    p1_ = reinterpret_cast<const unsigned char *>(img) + c1 * static_cast<int64_t>(sizeof(T));
+  }
+
+  // input row Y0 - R + t (clamped to the image) into load slot S
+  template <int S>
+  __device__ __forceinline__ void load(int64_t t) {
+    int64_t y = Y0 - R + t;
+    y = y < 0 ? 0 : (y >= H ? H - 1 : y);
+    raw0_[S] = *reinterpret_cast<const T *>(p0_ + y * pitch);
+    raw1_[S] = *reinterpret_cast<const T *>(p1_ + y * pitch);
+  }
+
+  template <int S>
+  __device__ __forceinline__ void step(int64_t t) {  // S = t % K
+    const uint32_t w = __byte_perm(raw0_[S], raw1_[S], 0x5410);  // (column 2l, 2l+1)
+    load<S>(t + K);
+    const uint32_t pv = __shfl_up_sync(kAll, w, 1), nx = __shfl_down_sync(kAll, w, 1);
+    win_[S][0] = pv;                         // columns -2, -1
+    win_[S][1] = __byte_perm(pv, w, 0x5432); // -1, 0
+    win_[S][2] = w;
+    win_[S][3] = __byte_perm(w, nx, 0x5432); //  1, 2
+    win_[S][4] = nx;                         //  2, 3
+    // centre row t - R of the window rows t - 2R .. t (ring slot (S + K - i) % K holds row t - i)
+    const int64_t yo = Y0 + t - 2 * R;
+    if (yo < Y0 || yo >= Y1) return;
+    constexpr int c = (S + K - R) % K;
+    const uint32_t *C = win_[c];
+    uint32_t h;
+    if constexpr (K == 5) {
+      const uint32_t *N2 = win_[(S + 1) % K], *N1 = win_[(S + 2) % K], *S1 = win_[(S + 4) % K], *S2 = win_[S];
+      const uint32_t plus = med9(C[0], C[1], C[2], C[3], C[4], N2[2], N1[2], S1[2], S2[2]);
+      const uint32_t cross = med9(N2[0], N1[1], C[2], S1[3], S2[4], N2[4], N1[3], S1[1], S2[0]);
+      h = med3(plus, cross, C[2]);
+    } else {
+      const uint32_t *N1 = win_[(S + 1) % K], *S1 = win_[S];
+      const uint32_t plus = med5(C[1], N1[2], C[2], S1[2], C[3]);
+      const uint32_t cross = med5(N1[1], N1[3], C[2], S1[1], S1[3]);
+      h = med3(plus, cross, C[2]);
+    }
+    if (lane < 1 || lane > 30 || x >= W) return;
+    unsigned char *d = out_ + yo * opitch + x * static_cast<int64_t>(sizeof(T));
+    *reinterpret_cast<T *>(d) = static_cast<T>(h & 0xFFFFu);
+    if (x + 1 < W) *reinterpret_cast<T *>(d + sizeof(T)) = static_cast<T>(h >> 16);
+  }
+
+  template <int... S>
+  __device__ __forceinline__ void steps(int64_t t0, std::integer_sequence<int, S...>) {
+    (step<S>(t0 + S), ...);
+  }
+  template <int... S>
+  __device__ __forceinline__ void loads(std::integer_sequence<int, S...>) {
+    (load<S>(S), ...);
+  }
+
+  __device__ void run() {
+    loads(std::make_integer_sequence<int, K>{});
+    const int64_t last = Y1 - Y0 + 2 * R;  // steps 0 .. last - 1 cover output rows Y0 .. Y1 - 1
+    for (int64_t t0 = 0; t0 < last; t0 += K) steps(t0, std::make_integer_sequence<int, K>{});
+  }
+};
+
+template <typename T, int K>
+__global__ void __launch_bounds__(32 * kHmfWarps) hmf_stream_kernel(const T *img, int64_t W, int64_t H,
+                                                                     int64_t pitch, T *out, int64_t out_pitch,
+                                                                     int64_t units_x, int64_t units) {
+  const int64_t unit = static_cast<int64_t>(blockIdx.x) * kHmfWarps + (threadIdx.x >> 5);
+  if (unit >= units) return;  // whole warps only
+  const int64_t ux = unit % units_x, uy = unit / units_x;
+  const int64_t Y0 = uy * kHmfUnitH, Y1 = Y0 + kHmfUnitH < H ? Y0 + kHmfUnitH : H;
+  HmfStrip<T, K> s(img, W, H, pitch, out, out_pitch, ux * kHmfOut, Y0, Y1);
+  s.run();
 }
 
 template <typename T>
-__global__ void __launch_bounds__(HNT) hmf_kernel(const T *img, int64_t W, int64_t H, int64_t pitch, T *out,
-                                                  int64_t out_pitch, int k, int64_t tiles_x) {
-  __shared__ int t[SH][SW + 1];
-  const int64_t tx = blockIdx.x % tiles_x, ty = blockIdx.x / tiles_x;
-  const int64_t x0 = tx * HW, y0 = ty * HH;
-  for (int i = threadIdx.x; i < SH * SW; i += HNT) {
-    const int ly = i / SW, lx = i % SW;
-    int64_t x = x0 - HR + lx, y = y0 - HR + ly;
-    x = x < 0 ? 0 : (x >= W ? W - 1 : x);
-    y = y < 0 ? 0 : (y >= H ? H - 1 : y);
-    t[ly][lx] = static_cast<int>(*reinterpret_cast<const T *>(reinterpret_cast<const unsigned char *>(img) +
-                                                              y * pitch + x * sizeof(T)));
-  }
-  __syncthreads();
-  for (int i = threadIdx.x; i < HW * HH; i += HNT) {
-    const int ly = i / HW, lx = i % HW;
-    const int64_t x = x0 + lx, y = y0 + ly;
-    if (x >= W || y >= H) continue;
-    const int cy = ly + HR, cx = lx + HR, c = t[cy][cx];
-    int plus, cross;
-    if (k == 5) {
-      plus = med9(t[cy][cx - 2], t[cy][cx - 1], c, t[cy][cx + 1], t[cy][cx + 2], t[cy - 2][cx],
-                  t[cy - 1][cx], t[cy + 1][cx], t[cy + 2][cx]);
-      cross = med9(t[cy - 2][cx - 2], t[cy - 1][cx - 1], c, t[cy + 1][cx + 1], t[cy + 2][cx + 2],
-                   t[cy - 2][cx + 2], t[cy - 1][cx + 1], t[cy + 1][cx - 1], t[cy + 2][cx - 2]);
-    } else {
-      plus = med5(t[cy][cx - 1], t[cy - 1][cx], c, t[cy + 1][cx], t[cy][cx + 1]);
-      cross = med5(t[cy - 1][cx - 1], t[cy - 1][cx + 1], c, t[cy + 1][cx - 1], t[cy + 1][cx + 1]);
-    }
-    *reinterpret_cast<T *>(reinterpret_cast<unsigned char *>(out) + y * out_pitch + x * sizeof(T)) =
-        static_cast<T>(med3(plus, cross, c));
-  }
+cudaError_t launch_hmf(const T *img, int64_t W, int64_t H, int64_t pitch, T *out, int64_t opitch, int k,
+                       cudaStream_t s) {
+  const int64_t units_x = (W + kHmfOut - 1) / kHmfOut, units = units_x * ((H + kHmfUnitH - 1) / kHmfUnitH);
+  const int64_t blocks = (units + kHmfWarps - 1) / kHmfWarps;
+  if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
+  const unsigned g = static_cast<unsigned>(blocks);
+  if (k == 5) hmf_stream_kernel<T, 5><<<g, 32 * kHmfWarps, 0, s>>>(img, W, H, pitch, out, opitch, units_x, units);
+  else hmf_stream_kernel<T, 3><<<g, 32 * kHmfWarps, 0, s>>>(img, W, H, pitch, out, opitch, units_x, units);
+  return cudaGetLastError();
 }
 
 }  // namespace
@@ -91,16 +190,11 @@ extern "C" fx_status fx_hybrid_median(const void *img, int64_t width, int64_t he
   const uintptr_t a0 = reinterpret_cast<uintptr_t>(img), a1 = a0 + (height - 1) * pitch_bytes + width * elem;
   const uintptr_t b0 = reinterpret_cast<uintptr_t>(out), b1 = b0 + (height - 1) * out_pitch_bytes + width * elem;
   if (a0 < b1 && b0 < a1) return FX_ERR_INVALID_ARG;
-  const int64_t tiles_x = (width + HW - 1) / HW, tiles = tiles_x * ((height + HH - 1) / HH);
-  if (tiles > 0x7fffffffLL) return FX_ERR_INVALID_ARG;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  if (dtype == FX_U8)
-    hmf_kernel<uint8_t><<<static_cast<unsigned>(tiles), HNT, 0, s>>>(
-        static_cast<const uint8_t *>(img), width, height, pitch_bytes, static_cast<uint8_t *>(out), out_pitch_bytes,
-        window, tiles_x);
-  else
-    hmf_kernel<uint16_t><<<static_cast<unsigned>(tiles), HNT, 0, s>>>(
-        static_cast<const uint16_t *>(img), width, height, pitch_bytes, static_cast<uint16_t *>(out),
-        out_pitch_bytes, window, tiles_x);
-  return cudaGetLastError() == cudaSuccess ? FX_OK : FX_ERR_CUDA;
+  const cudaError_t e =
+      dtype == FX_U8 ? launch_hmf(static_cast<const uint8_t *>(img), width, height, pitch_bytes,
+                                  static_cast<uint8_t *>(out), out_pitch_bytes, window, s)
+                     : launch_hmf(static_cast<const uint16_t *>(img), width, height, pitch_bytes,
+                                  static_cast<uint16_t *>(out), out_pitch_bytes, window, s);
+  return e == cudaSuccess ? FX_OK : FX_ERR_CUDA;
 }

@@ -40,3 +40,18 @@ def test_hmf_pitched_and_errors(cuda_lib):
     t = torch.zeros((8, 8), dtype=torch.uint16, device="cuda")
     assert lib.fx_hybrid_median(t.data_ptr(), 8, 8, 16, 2, 4, obuf.data_ptr(), 0, None) == 1
     assert lib.fx_hybrid_median(t.data_ptr(), 8, 8, 16, 2, 5, t.data_ptr(), 0, None) == 1
+
+
+@pytest.mark.parametrize("window", [3, 5])
+@pytest.mark.parametrize("shape,bits", [((777, 1001), 12), ((600, 61), 8), ((257, 123), 16)])
+def test_hmf_multi_unit(cuda_lib, window, shape, bits):
+    """Images spanning several 256-row units and 60-column strips (odd widths,
+    a width one above a strip), against the oracle."""
+    h, w = shape
+    if bits == 16:
+        img = np.random.default_rng(w).integers(0, 65536, size=shape).astype(np.uint16)
+    else:
+        img = scenes.scene(w, h, seed=w + h, n_rects=40, noise_sigma=4.0 * (1 << (bits - 8)),
+                           impulse_frac=0.05, bits=bits)
+    got = cuda_lib.hybrid_median(torch.from_numpy(img).cuda(), window).cpu().numpy()
+    assert np.array_equal(got, oracle.hybrid_median(img, window))
