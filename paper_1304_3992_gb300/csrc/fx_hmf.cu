@@ -64,15 +64,20 @@ __device__ __forceinline__ uint32_t med9(uint32_t a0, uint32_t a1, uint32_t a2, 
   return med3(vmax(vmax(al, bl), cl), med3(am, bm, cm), vmin(vmin(ah, bh), ch));
 }
 
-template <typename T, int K>
+// kPair: one aligned load of the lane's two pixels per row (base and pitch
+// multiples of two pixels, even width), the clamped columns picked by a byte
+// selector at use; otherwise two single-pixel loads at the clamped columns.
+template <typename T, int K, bool kPair>
 struct HmfStrip {
   static constexpr int R = K / 2;
-  const unsigned char *p0_, *p1_;  // this lane's two clamped columns in image row 0
+  static constexpr int L = K;  // loads run one window (k rows) ahead
+  const unsigned char *p0_, *p1_;  // this lane's load addresses in image row 0
+  uint32_t sel_;
   int64_t pitch, H, Y0, Y1, W, x;
   unsigned char *out_;
   int64_t opitch;
   int lane;
-  uint32_t raw0_[K], raw1_[K];  // loaded pixels of the next K rows
+  uint32_t raw0_[L], raw1_[L];  // loaded pixels of the next L rows
   uint32_t win_[K][5];          // per ring row: the pair words shifted by -2..2 columns
 
   __device__ HmfStrip(const T *img, int64_t W_, int64_t H_, int64_t pitch_, T *out, int64_t opitch_, int64_t X0,
@@ -82,8 +87,17 @@ struct HmfStrip {
     lane = threadIdx.x & 31;
     x = X0 - 2 + 2 * lane;
     const int64_t c0 = x < 0 ? 0 : (x >= W ? W - 1 : x), c1 = x + 1 < 0 ? 0 : (x + 1 >= W ? W - 1 : x + 1);
-    p0_ = reinterpret_cast<const unsigned char *>(img) + c0 * static_cast<int64_t>(sizeof(T));
-    p1_ = reinterpret_cast<const unsigned char *>(img) + c1 * static_cast<int64_t>(sizeof(T));
+    if constexpr (kPair) {
+      const int64_t cb = (c0 < W - 2 ? c0 : W - 2) & ~int64_t{1};  // even pair holding both columns
+      p0_ = p1_ = reinterpret_cast<const unsigned char *>(img) + cb * static_cast<int64_t>(sizeof(T));
+      const uint32_t h0 = static_cast<uint32_t>(c0 - cb), h1 = static_cast<uint32_t>(c1 - cb);
+      if constexpr (sizeof(T) == 2) sel_ = (h0 ? 0x32u : 0x10u) | ((h1 ? 0x32u : 0x10u) << 8);
+      else sel_ = h0 | 0x40u | (h1 << 8) | 0x4000u;
+    } else {
+      p0_ = reinterpret_cast<const unsigned char *>(img) + c0 * static_cast<int64_t>(sizeof(T));
+      p1_ = reinterpret_cast<const unsigned char *>(img) + c1 * static_cast<int64_t>(sizeof(T));
+      sel_ = 0x5410u;
+    }
   }
 
   // input row Y0 - R + t (clamped to the image) into load slot S
@@ -91,14 +105,21 @@ struct HmfStrip {
   __device__ __forceinline__ void load(int64_t t) {
     int64_t y = Y0 - R + t;
     y = y < 0 ? 0 : (y >= H ? H - 1 : y);
-    raw0_[S] = *reinterpret_cast<const T *>(p0_ + y * pitch);
-    raw1_[S] = *reinterpret_cast<const T *>(p1_ + y * pitch);
+    if constexpr (kPair) {
+      if constexpr (sizeof(T) == 2) raw0_[S] = __ldg(reinterpret_cast<const uint32_t *>(p0_ + y * pitch));
+      else raw0_[S] = __ldg(reinterpret_cast<const uint16_t *>(p0_ + y * pitch));
+    } else {
+      raw0_[S] = __ldg(reinterpret_cast<const T *>(p0_ + y * pitch));
+      raw1_[S] = __ldg(reinterpret_cast<const T *>(p1_ + y * pitch));
+    }
   }
 
-  template <int S>
-  __device__ __forceinline__ void step(int64_t t) {  // S = t % K
-    const uint32_t w = __byte_perm(raw0_[S], raw1_[S], 0x5410);  // (column 2l, 2l+1)
-    load<S>(t + K);
+  template <int SL>
+  __device__ __forceinline__ void step(int64_t t) {  // SL = t % L; window slot S = t % K
+    constexpr int S = SL % K;
+    // (column 2l, 2l+1) as a u16x2 word; the selection also copies the slot before it is refilled
+    const uint32_t w = kPair ? __byte_perm(raw0_[SL], 0, sel_) : __byte_perm(raw0_[SL], raw1_[SL], 0x5410);
+    load<SL>(t + L);
     const uint32_t pv = __shfl_up_sync(kAll, w, 1), nx = __shfl_down_sync(kAll, w, 1);
     win_[S][0] = pv;                         // columns -2, -1
     win_[S][1] = __byte_perm(pv, w, 0x5432); // -1, 0
@@ -138,13 +159,13 @@ struct HmfStrip {
   }
 
   __device__ void run() {
-    loads(std::make_integer_sequence<int, K>{});
+    loads(std::make_integer_sequence<int, L>{});
     const int64_t last = Y1 - Y0 + 2 * R;  // steps 0 .. last - 1 cover output rows Y0 .. Y1 - 1
-    for (int64_t t0 = 0; t0 < last; t0 += K) steps(t0, std::make_integer_sequence<int, K>{});
+    for (int64_t t0 = 0; t0 < last; t0 += L) steps(t0, std::make_integer_sequence<int, L>{});
   }
 };
 
-template <typename T, int K>
+template <typename T, int K, bool kPair>
 __global__ void __launch_bounds__(32 * kHmfWarps) hmf_stream_kernel(const T *img, int64_t W, int64_t H,
                                                                      int64_t pitch, T *out, int64_t out_pitch,
                                                                      int64_t units_x, int64_t units) {
@@ -152,7 +173,7 @@ __global__ void __launch_bounds__(32 * kHmfWarps) hmf_stream_kernel(const T *img
   if (unit >= units) return;  // whole warps only
   const int64_t ux = unit % units_x, uy = unit / units_x;
   const int64_t Y0 = uy * kHmfUnitH, Y1 = Y0 + kHmfUnitH < H ? Y0 + kHmfUnitH : H;
-  HmfStrip<T, K> s(img, W, H, pitch, out, out_pitch, ux * kHmfOut, Y0, Y1);
+  HmfStrip<T, K, kPair> s(img, W, H, pitch, out, out_pitch, ux * kHmfOut, Y0, Y1);
   s.run();
 }
 
@@ -163,8 +184,16 @@ cudaError_t launch_hmf(const T *img, int64_t W, int64_t H, int64_t pitch, T *out
   const int64_t blocks = (units + kHmfWarps - 1) / kHmfWarps;
   if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
   const unsigned g = static_cast<unsigned>(blocks);
-  if (k == 5) hmf_stream_kernel<T, 5><<<g, 32 * kHmfWarps, 0, s>>>(img, W, H, pitch, out, opitch, units_x, units);
-  else hmf_stream_kernel<T, 3><<<g, 32 * kHmfWarps, 0, s>>>(img, W, H, pitch, out, opitch, units_x, units);
+  constexpr int nt = 32 * kHmfWarps;
+  const int64_t two = 2 * static_cast<int64_t>(sizeof(T));
+  const bool pair = reinterpret_cast<uintptr_t>(img) % two == 0 && pitch % two == 0 && W % 2 == 0;
+  if (k == 5) {
+    if (pair) hmf_stream_kernel<T, 5, true><<<g, nt, 0, s>>>(img, W, H, pitch, out, opitch, units_x, units);
+    else hmf_stream_kernel<T, 5, false><<<g, nt, 0, s>>>(img, W, H, pitch, out, opitch, units_x, units);
+  } else {
+    if (pair) hmf_stream_kernel<T, 3, true><<<g, nt, 0, s>>>(img, W, H, pitch, out, opitch, units_x, units);
+    else hmf_stream_kernel<T, 3, false><<<g, nt, 0, s>>>(img, W, H, pitch, out, opitch, units_x, units);
+  }
   return cudaGetLastError();
 }
 
