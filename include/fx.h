@@ -220,8 +220,9 @@ fx_status fx_get_device_status(fx_plan *plan, void *stream);
 
 /*
  * End-to-end call on HOST buffers: copies the image to the device in row
- * bands, extracts, and copies the mask back, overlapping the copies of one
- * band with the kernel of the previous one on the plan's own streams.  Host
+ * chunks of about 64 MiB, extracts, and copies the mask back; the upload of a
+ * chunk, the kernel of the previous one and the download of the one before
+ * run at the same time on the plan's own streams (three staging slots).  Host
  * buffers should be page-locked for full copy speed.  Synchronous: the mask
  * is in out_mask_host when the call returns.  The plan grows its staging
  * buffers on first use.
@@ -230,6 +231,15 @@ fx_status fx_get_device_status(fx_plan *plan, void *stream);
 fx_status fx_extract_host(fx_plan *plan, const void *img_host, int64_t width, int64_t height,
                           int64_t pitch_bytes, fx_dtype dtype, uint8_t *out_mask_host,
                           int64_t out_pitch);
+
+/*
+ * fx_extract_host for n images in one call (descs[i].img and .out_mask are
+ * HOST pointers here): the row chunks of all images share one copy / kernel /
+ * copy pipeline, so uploads of the next image overlap the work on the
+ * previous one.  Synchronous; descs is read before the call returns.
+ * Errors: as fx_extract_host (n < 1 or a bad descriptor: FX_ERR_INVALID_ARG).
+ */
+fx_status fx_extract_host_batch(fx_plan *plan, const fx_image_desc *descs, int32_t n);
 
 /*
  * The hybrid median filter of Sec. 3.4 on its own, applied to a uint8/uint16

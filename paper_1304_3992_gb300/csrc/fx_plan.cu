@@ -175,6 +175,10 @@ const void *redo_kernel_of(const KParams &kp) {
 
 using namespace fx;
 
+// Staging slots of the host-buffer path: copy-in, kernel and copy-out of three
+// consecutive row chunks run at the same time.
+constexpr int kHostSlots = 3;
+
 struct fx_plan {
   fx_params params;
   KParams kp8, kp16;
@@ -193,10 +197,11 @@ struct fx_plan {
   size_t smem;
   // end-to-end path on host buffers
   cudaStream_t s_h2d, s_comp, s_d2h;
-  void *d_in[2];
-  uint8_t *d_out[2];
+  // host-buffer path: a ring of kHostSlots staging buffers and their events
+  void *d_in[kHostSlots];
+  uint8_t *d_out[kHostSlots];
   size_t in_cap, out_cap;
-  cudaEvent_t ev_in[2], ev_comp[2], ev_out[2];
+  cudaEvent_t ev_in[kHostSlots], ev_comp[kHostSlots], ev_out[kHostSlots];
 };
 
 namespace {
@@ -337,7 +342,7 @@ fx_status fill_table(fx_plan *p, unsigned char *h, const fx_image_desc *d, int32
 }
 
 void free_host_path(fx_plan *p) {
-  for (int i = 0; i < 2; ++i) {
+  for (int i = 0; i < kHostSlots; ++i) {
     if (p->d_in[i]) cudaFree(p->d_in[i]);
     if (p->d_out[i]) cudaFree(p->d_out[i]);
     p->d_in[i] = nullptr;
@@ -391,7 +396,7 @@ fx_status fx_plan_create(fx_plan **out, const fx_params *params, int32_t max_ima
   ok = ok && cudaStreamCreateWithFlags(&p->s_h2d, cudaStreamNonBlocking) == cudaSuccess &&
        cudaStreamCreateWithFlags(&p->s_comp, cudaStreamNonBlocking) == cudaSuccess &&
        cudaStreamCreateWithFlags(&p->s_d2h, cudaStreamNonBlocking) == cudaSuccess;
-  for (int i = 0; i < 2 && ok; ++i)
+  for (int i = 0; i < kHostSlots && ok; ++i)
     ok = cudaEventCreateWithFlags(&p->ev_in[i], cudaEventDisableTiming) == cudaSuccess &&
          cudaEventCreateWithFlags(&p->ev_comp[i], cudaEventDisableTiming) == cudaSuccess &&
          cudaEventCreateWithFlags(&p->ev_out[i], cudaEventDisableTiming) == cudaSuccess;
@@ -416,6 +421,8 @@ fx_status fx_plan_destroy(fx_plan *p) {
   for (int i = 0; i < 2; ++i) {
     if (p->h_table[i]) cudaFreeHost(p->h_table[i]);
     if (p->h_free[i]) cudaEventDestroy(p->h_free[i]);
+  }
+  for (int i = 0; i < kHostSlots; ++i) {
     if (p->ev_in[i]) cudaEventDestroy(p->ev_in[i]);
     if (p->ev_comp[i]) cudaEventDestroy(p->ev_comp[i]);
     if (p->ev_out[i]) cudaEventDestroy(p->ev_out[i]);
@@ -514,35 +521,45 @@ fx_status fx_get_device_status(fx_plan *p, void *stream) {
   return h == 0 ? FX_OK : FX_ERR_INVALID_ARG;
 }
 
-// Host buffers in, host mask out.  The image goes to the device in row bands;
-// band k+1's upload overlaps band k's kernel and band k-1's download.  Each band
-// carries the input halo rows its outputs need, so results equal fx_extract's.
-fx_status fx_extract_host(fx_plan *p, const void *img_host, int64_t width, int64_t height,
-                          int64_t pitch_bytes, fx_dtype dtype, uint8_t *out_host, int64_t out_pitch) {
-  if (!p || !img_host || !out_host) return FX_ERR_INVALID_ARG;
-  if (dtype != FX_U8 && dtype != FX_U16) return FX_ERR_INVALID_ARG;
-  const int64_t elem = dtype == FX_U8 ? 1 : 2;
-  if (out_pitch == 0) out_pitch = width;
-  if (width < 1 || height < 1 || width > (1LL << 30) || height > (1LL << 30) ||
-      pitch_bytes < width * elem || pitch_bytes % elem || out_pitch < width)
-    return FX_ERR_INVALID_ARG;
-  if (dtype == FX_U16 && p->st16 != FX_OK) return p->st16;
-  const KParams &kp = dtype == FX_U8 ? p->kp8 : p->kp16;
+}  // extern "C"
+
+namespace {
+
+// Host buffers in, host mask out.  Images go to the device in row chunks;
+// chunk k+1's upload overlaps chunk k's kernel and chunk k-1's download, across
+// image boundaries.  Each chunk carries the input halo rows its outputs need,
+// so results equal fx_extract's.
+struct HostJob {  // one image of the host-buffer path
+  const unsigned char *src;
+  int64_t width, height, pitch, elem;
+  uint8_t *dst;
+  int64_t out_pitch;
+};
+
+// Rows per chunk: about 64 MiB of input (enough strips to fill the GPU, small
+// enough that copies and kernels of neighbouring chunks overlap), >= 64 rows.
+int64_t chunk_rows(const HostJob &j) {
+  const int64_t dpitch = (j.width * j.elem + 255) / 256 * 256;
+  return std::min(j.height, std::max<int64_t>(64, (64LL << 20) / dpitch));
+}
+
+// All chunks of all images through the slot ring: the copy-in of a chunk, the
+// kernel of the one before and the copy-out of the one before that overlap.
+fx_status host_pipeline(fx_plan *p, const HostJob *jobs, int32_t n) {
   if (cudaSetDevice(p->device) != cudaSuccess) return FX_ERR_CUDA;
-  const int64_t r = kp.r_in;
-  const int64_t dpitch = (width * elem + 255) / 256 * 256;
-  // bands of ~256 MiB of input (enough strips to fill the GPU), at least 64 rows
-  int64_t band = std::max<int64_t>(64, (256LL << 20) / dpitch);
-  band = std::min(band, height);
-  const int64_t in_rows = std::min(height, band + 2 * r);
-  const size_t need_in = static_cast<size_t>(in_rows * dpitch);
-  const size_t need_out = static_cast<size_t>(band * width);
+  size_t need_in = 0, need_out = 0;
+  for (int32_t i = 0; i < n; ++i) {
+    const KParams &kp = jobs[i].elem == 1 ? p->kp8 : p->kp16;
+    const int64_t dpitch = (jobs[i].width * jobs[i].elem + 255) / 256 * 256, band = chunk_rows(jobs[i]);
+    need_in = std::max(need_in, static_cast<size_t>(std::min(jobs[i].height, band + 2 * kp.r_in) * dpitch));
+    need_out = std::max(need_out, static_cast<size_t>(band * jobs[i].width));
+  }
   if (need_in > p->in_cap || need_out > p->out_cap) {
     cudaStreamSynchronize(p->s_h2d);
     cudaStreamSynchronize(p->s_comp);
     cudaStreamSynchronize(p->s_d2h);
     free_host_path(p);
-    for (int i = 0; i < 2; ++i)
+    for (int i = 0; i < kHostSlots; ++i)
       if (cudaMalloc(&p->d_in[i], need_in) != cudaSuccess || cudaMalloc(&p->d_out[i], need_out) != cudaSuccess) {
         free_host_path(p);
         return FX_ERR_NOMEM;
@@ -550,37 +567,90 @@ fx_status fx_extract_host(fx_plan *p, const void *img_host, int64_t width, int64
     p->in_cap = need_in;
     p->out_cap = need_out;
   }
-  const unsigned char *src = static_cast<const unsigned char *>(img_host);
   cudaError_t e = cudaSuccess;
   int k = 0;
-  for (int64_t y0 = 0; y0 < height && e == cudaSuccess; y0 += band, ++k) {
-    const int slot = k & 1;
-    const int64_t y1 = std::min(height, y0 + band);
-    const int64_t a = std::max<int64_t>(0, y0 - r), b = std::min(height, y1 + r);
-    // slot reuse: the kernel two bands ago must be done reading d_in[slot], and
-    // the download two bands ago done reading d_out[slot]
-    e = cudaStreamWaitEvent(p->s_h2d, p->ev_comp[slot], 0);
-    if (e == cudaSuccess)
-      e = cudaMemcpy2DAsync(p->d_in[slot], dpitch, src + a * pitch_bytes, pitch_bytes, width * elem, b - a,
-                            cudaMemcpyHostToDevice, p->s_h2d);
-    if (e == cudaSuccess) e = cudaEventRecord(p->ev_in[slot], p->s_h2d);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(p->s_comp, p->ev_in[slot], 0);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(p->s_comp, p->ev_out[slot], 0);
-    if (e == cudaSuccess) {
-      ImageView v{p->d_in[slot], width, height, dpitch, a, static_cast<int32_t>(elem), p->d_out[slot], width, y0, y1, b};
-      e = launch_extract(v, kp, p->s_comp);
+  for (int32_t i = 0; i < n && e == cudaSuccess; ++i) {
+    const HostJob &jb = jobs[i];
+    const KParams &kp = jb.elem == 1 ? p->kp8 : p->kp16;
+    const int64_t r = kp.r_in, width = jb.width, height = jb.height, elem = jb.elem;
+    const int64_t dpitch = (width * elem + 255) / 256 * 256, band = chunk_rows(jb);
+    for (int64_t y0 = 0; y0 < height && e == cudaSuccess; y0 += band, ++k) {
+      const int slot = k % kHostSlots;
+      const int64_t y1 = std::min(height, y0 + band);
+      const int64_t a = std::max<int64_t>(0, y0 - r), b = std::min(height, y1 + r);
+      // slot reuse: the kernel kHostSlots chunks ago must be done reading
+      // d_in[slot], and its copy-out done reading d_out[slot]
+      e = cudaStreamWaitEvent(p->s_h2d, p->ev_comp[slot], 0);
+      if (e == cudaSuccess) {
+        if (jb.pitch == dpitch)  // contiguous rows: one linear copy
+          e = cudaMemcpyAsync(p->d_in[slot], jb.src + a * jb.pitch, (b - a) * dpitch, cudaMemcpyHostToDevice,
+                              p->s_h2d);
+        else
+          e = cudaMemcpy2DAsync(p->d_in[slot], dpitch, jb.src + a * jb.pitch, jb.pitch, width * elem, b - a,
+                                cudaMemcpyHostToDevice, p->s_h2d);
+      }
+      if (e == cudaSuccess) e = cudaEventRecord(p->ev_in[slot], p->s_h2d);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(p->s_comp, p->ev_in[slot], 0);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(p->s_comp, p->ev_out[slot], 0);
+      if (e == cudaSuccess) {
+        ImageView v{p->d_in[slot], width, height, dpitch, a, static_cast<int32_t>(elem), p->d_out[slot], width,
+                    y0, y1, b};
+        e = launch_extract(v, kp, p->s_comp);
+      }
+      if (e == cudaSuccess) e = cudaEventRecord(p->ev_comp[slot], p->s_comp);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(p->s_d2h, p->ev_comp[slot], 0);
+      if (e == cudaSuccess) {
+        if (jb.out_pitch == width)
+          e = cudaMemcpyAsync(jb.dst + y0 * jb.out_pitch, p->d_out[slot], (y1 - y0) * width, cudaMemcpyDeviceToHost,
+                              p->s_d2h);
+        else
+          e = cudaMemcpy2DAsync(jb.dst + y0 * jb.out_pitch, jb.out_pitch, p->d_out[slot], width, width, y1 - y0,
+                                cudaMemcpyDeviceToHost, p->s_d2h);
+      }
+      if (e == cudaSuccess) e = cudaEventRecord(p->ev_out[slot], p->s_d2h);
     }
-    if (e == cudaSuccess) e = cudaEventRecord(p->ev_comp[slot], p->s_comp);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(p->s_d2h, p->ev_comp[slot], 0);
-    if (e == cudaSuccess)
-      e = cudaMemcpy2DAsync(out_host + y0 * out_pitch, out_pitch, p->d_out[slot], width, width, y1 - y0,
-                            cudaMemcpyDeviceToHost, p->s_d2h);
-    if (e == cudaSuccess) e = cudaEventRecord(p->ev_out[slot], p->s_d2h);
   }
   cudaError_t e2 = cudaStreamSynchronize(p->s_d2h);
   cudaStreamSynchronize(p->s_comp);
   cudaStreamSynchronize(p->s_h2d);
   return (e == cudaSuccess && e2 == cudaSuccess) ? FX_OK : FX_ERR_CUDA;
+}
+
+fx_status host_job(fx_plan *p, const void *img_host, int64_t width, int64_t height, int64_t pitch_bytes,
+                   int32_t dtype, uint8_t *out_host, int64_t out_pitch, HostJob *j) {
+  if (!img_host || !out_host) return FX_ERR_INVALID_ARG;
+  if (dtype != FX_U8 && dtype != FX_U16) return FX_ERR_INVALID_ARG;
+  const int64_t elem = dtype == FX_U8 ? 1 : 2;
+  if (out_pitch == 0) out_pitch = width;
+  if (width < 1 || height < 1 || width > (1LL << 30) || height > (1LL << 30) || pitch_bytes < width * elem ||
+      pitch_bytes % elem || pitch_bytes > 0xFFFFFFFFLL || out_pitch < width || out_pitch > 0xFFFFFFFFLL)
+    return FX_ERR_INVALID_ARG;
+  if (dtype == FX_U16 && p->st16 != FX_OK) return p->st16;
+  *j = HostJob{static_cast<const unsigned char *>(img_host), width, height, pitch_bytes, elem, out_host, out_pitch};
+  return FX_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+fx_status fx_extract_host(fx_plan *p, const void *img_host, int64_t width, int64_t height,
+                          int64_t pitch_bytes, fx_dtype dtype, uint8_t *out_host, int64_t out_pitch) {
+  if (!p) return FX_ERR_INVALID_ARG;
+  HostJob j;
+  fx_status st = host_job(p, img_host, width, height, pitch_bytes, dtype, out_host, out_pitch, &j);
+  return st != FX_OK ? st : host_pipeline(p, &j, 1);
+}
+
+fx_status fx_extract_host_batch(fx_plan *p, const fx_image_desc *descs, int32_t n) {
+  if (!p || !descs || n < 1) return FX_ERR_INVALID_ARG;
+  std::vector<HostJob> jobs(static_cast<size_t>(n));
+  for (int32_t i = 0; i < n; ++i) {
+    fx_status st = host_job(p, descs[i].img, descs[i].width, descs[i].height, descs[i].pitch_bytes, descs[i].dtype,
+                            descs[i].out_mask, descs[i].out_pitch, &jobs[static_cast<size_t>(i)]);
+    if (st != FX_OK) return st;
+  }
+  return host_pipeline(p, jobs.data(), n);
 }
 
 }  // extern "C"

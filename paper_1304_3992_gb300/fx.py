@@ -79,6 +79,7 @@ _SIGNATURES = {
     "fx_get_device_status": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "fx_extract_host": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
                                        ctypes.c_int64, ctypes.c_int, ctypes.c_void_p, ctypes.c_int64]),
+    "fx_extract_host_batch": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ImageDesc), ctypes.c_int32]),
     "fx_extract_batch_noalloc": (ctypes.c_int, [ctypes.POINTER(Params), ctypes.POINTER(ImageDesc),
                                                 ctypes.c_int32, ctypes.c_void_p]),
     "fx_hybrid_median": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
@@ -282,3 +283,19 @@ class Plan:
         _check(self._lib.fx_extract_host(self._h, img_np.ctypes.data, w, h, img_np.strides[0], dt,
                                          out_np.ctypes.data, out_np.strides[0]), "fx_extract_host")
         return out_np
+
+    def extract_host_batch(self, pairs):
+        """fx_extract_host_batch on a list of (image, mask) host numpy arrays
+        (2-D, contiguous rows); the masks are filled in place."""
+        import numpy as np
+        arr = (ImageDesc * len(pairs))()
+        for i, (img, out) in enumerate(pairs):
+            if img.ndim != 2 or img.strides[1] != img.itemsize or out.shape != img.shape or out.dtype != np.uint8:
+                raise ValueError("pairs must be 2-D images with contiguous rows and uint8 masks of the same shape")
+            dt = FX_U8 if img.dtype == np.uint8 else FX_U16 if img.dtype == np.uint16 else None
+            if dt is None:
+                raise TypeError(img.dtype)
+            arr[i].img, arr[i].width, arr[i].height, arr[i].pitch_bytes = img.ctypes.data, img.shape[1], img.shape[0], img.strides[0]
+            arr[i].dtype, arr[i].out_mask, arr[i].out_pitch = dt, out.ctypes.data, out.strides[0]
+        _check(self._lib.fx_extract_host_batch(self._h, arr, len(pairs)), "fx_extract_host_batch")
+        return [out for _, out in pairs]

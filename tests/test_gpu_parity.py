@@ -293,3 +293,25 @@ def test_crossing_map_source_streaming(cuda_lib, hmf):
         plan.extract_batch(pairs)
         torch.cuda.synchronize()
         assert_same(pairs[0][1].cpu().numpy(), ref, f"batched hmf {hmf}")
+
+
+def test_extract_host_batch_matches_device(cuda_lib):
+    """fx_extract_host_batch: several host images (contiguous rows -> linear
+    copies, padded rows -> pitched copies, both dtypes, one image of several
+    chunks) through one pipeline, each equal to the device path."""
+    imgs = [scenes.scene(1500, 1300, seed=41, n_rects=200, noise_sigma=24, impulse_frac=0.005, bits=12),
+            scenes.scene(999, 700, seed=42, n_rects=90, noise_sigma=4, impulse_frac=0.01, bits=8),
+            scenes.scene(4096, 9000, seed=43, n_rects=900, noise_sigma=24, impulse_frac=0.005, bits=12)]
+    padded = scenes.pitched(imgs[1], 1280)
+    hosts = [imgs[0], padded, imgs[2]]
+    _, p = pair(16.0)
+    outs = [np.full(h.shape, 9, np.uint8) for h in hosts]
+    with cuda_lib.Plan(p, max_images=4) as plan:
+        plan.extract_host_batch(list(zip(hosts, outs)))
+        for i, (h, o) in enumerate(zip(hosts, outs)):
+            assert_same(o, run(cuda_lib, np.ascontiguousarray(h), p), f"host batch image {i}")
+        # a second call reuses the staging buffers
+        outs2 = [np.zeros_like(o) for o in outs]
+        plan.extract_host_batch(list(zip(hosts, outs2)))
+        for o, o2 in zip(outs, outs2):
+            assert_same(o2, o, "second call")
