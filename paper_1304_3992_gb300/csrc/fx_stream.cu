@@ -1,4 +1,6 @@
 // fx_stream.cu -- grid launch of the streaming fast path (fx_stream.cuh).
+#include <cstdint>
+
 #include "fx_stream.cuh"
 
 namespace fx {
@@ -64,10 +66,45 @@ bool pair_loads_ok(const ImageView &v) {
   return reinterpret_cast<uintptr_t>(v.img) % two == 0 && v.pitch % two == 0 && v.width % 2 == 0;
 }
 
+// Resident warps of the streaming kernel on the current device (3 CTAs of 4
+// warps per SM), cached per device.
+int64_t warp_slots() {
+  static int64_t slots[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 152 * 12;
+  if (!slots[dev]) {
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 152;
+    slots[dev] = static_cast<int64_t>(sms) * 3 * kWarpsPerCta;
+  }
+  return slots[dev];
+}
+
+// Unit height (rows per warp) for an image of `rows` output rows and `units_x`
+// strips: a unit walks uh + overhead rows (ring prefill and pipeline delay), and
+// the launch takes about ceil(units / resident warps) unit times, so small
+// images get short units (parallelism) and large ones long units (less
+// overhead).  Heights are multiples of 16 up to 768.
+int unit_height(int64_t rows, int64_t units_x, const KParams &kp) {
+  const int64_t slots = warp_slots();
+  const int64_t overhead = 56 + 16 * ((kp.nhmf == 2 ? 1 : 0) + (kp.source == 1 ? 1 : 0));
+  int best = 768;
+  int64_t best_cost = INT64_MAX;
+  for (int uh = 768; uh >= 16; uh -= 16) {
+    const int64_t units = units_x * ((rows + uh - 1) / uh);
+    const int64_t cost = (units + slots - 1) / slots * (uh + overhead);
+    if (cost < best_cost) {
+      best_cost = cost;
+      best = uh;
+    }
+  }
+  return best;
+}
+
 cudaError_t launch_fast(const ImageView &v, const KParams &kp, cudaStream_t s) {
-  const int uh = kDefaultUnitH;
   const int uw = strip_width(kp.source == 1);
   const int64_t units_x = (v.width + uw - 1) / uw;
+  const int uh = unit_height(v.y_end - v.y_begin, units_x, kp);
   const int64_t units_y = (v.y_end - v.y_begin + uh - 1) / uh;
   const int64_t units = units_x * units_y;
   if (units <= 0) return cudaSuccess;
