@@ -199,7 +199,10 @@ fx_status fx_extract_batch(fx_plan *plan, const fx_image_desc *descs, int32_t n,
  * tile_w must be the strip width of the streaming kernel (52, or 48 when the
  * standard deviation is taken over the crossing map) and tile_h a multiple
  * of 16 in [16, 8192]; ctas_per_sm is in 1..8 (4 warps per CTA).
- * fx_plan_autotune times the heights {256, 512, 1024, 2048} x every
+ * Until one of the two calls below fixes the shape, a plan picks the unit
+ * height for each batch itself (multiples of 16 up to 768, from the batch's
+ * unit count against the resident warps; 3 CTAs per SM).
+ * fx_plan_autotune times the heights {256, 512, 768, 1024} x every
  * CTAs-per-SM count the kernel's occupancy allows on the given images (their
  * outputs are overwritten) and keeps the fastest; fx_plan_set_tile forces
  * one.  Plans whose parameters need the general kernel (median windows whose

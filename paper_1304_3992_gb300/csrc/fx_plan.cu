@@ -194,6 +194,7 @@ struct fx_plan {
   int *d_status;
   cudaGraphExec_t graph[2];
   int unit_w, unit_h, ctas_per_sm;
+  bool auto_h;  // pick the unit height per call (until fx_plan_set_tile fixes it)
   size_t smem;
   // end-to-end path on host buffers
   cudaStream_t s_h2d, s_comp, s_d2h;
@@ -288,8 +289,27 @@ fx_status rebuild(fx_plan *p) {
 fx_status fill_table(fx_plan *p, unsigned char *h, const fx_image_desc *d, int32_t n) {
   BatchHeader *hdr = reinterpret_cast<BatchHeader *>(h);
   BatchImage *ims = reinterpret_cast<BatchImage *>(h + sizeof(BatchHeader));
-  const int uw = p->fast ? p->unit_w : gen::TW, uh = p->fast ? p->unit_h : gen::TH;
   const int uwx = p->fast ? strip_width(p->kp8.source == 1) : gen::TW;  // output columns per unit
+  int uh = p->fast ? p->unit_h : gen::TH;
+  if (p->fast && p->auto_h) {
+    // the wave model of fx_extract over the whole batch: a warp walks uh rows
+    // plus the pipeline overhead, and the batch takes about ceil(units / warps)
+    // unit times
+    const int64_t slots = static_cast<int64_t>(p->num_sms) * p->ctas_per_sm * kWarpsPerCta;
+    const int64_t overhead = 56 + 16 * ((p->kp8.nhmf == 2 ? 1 : 0) + (p->kp8.source == 1 ? 1 : 0));
+    int64_t best_cost = INT64_MAX;
+    for (int h = 768; h >= 16; h -= 16) {
+      int64_t units = 0;
+      for (int32_t i = 0; i < n; ++i)
+        units += std::max<int64_t>(1, (d[i].width + uwx - 1) / uwx) * std::max<int64_t>(1, (d[i].height + h - 1) / h);
+      const int64_t cost = (units + slots - 1) / slots * (h + overhead);
+      if (cost < best_cost) {
+        best_cost = cost;
+        uh = h;
+      }
+    }
+  }
+  const int uw = p->fast ? p->unit_w : gen::TW;
   int64_t total = 0, pair_units = 0;
   // On the streaming path the queue runs through the images in four groups:
   // one aligned load per lane (uint16, then uint8), then pixel by pixel (uint16,
@@ -380,7 +400,8 @@ fx_status fx_plan_create(fx_plan **out, const fx_params *params, int32_t max_ima
   p->max_images = max_images;
   p->unit_w = strip_width(p->kp8.source == 1);
   p->unit_h = kDefaultUnitH;
-  p->ctas_per_sm = 2;
+  p->ctas_per_sm = p->fast ? 3 : 2;
+  p->auto_h = true;
   if (cudaSetDevice(device) != cudaSuccess || cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
     delete p;
     return FX_ERR_CUDA;
@@ -461,6 +482,7 @@ fx_status fx_plan_set_tile(fx_plan *p, int32_t tile_w, int32_t tile_h, int32_t c
   p->unit_w = tile_w;
   p->unit_h = tile_h;
   p->ctas_per_sm = ctas_per_sm;
+  p->auto_h = false;
   return rebuild(p);
 }
 

@@ -45,7 +45,7 @@ constexpr int kDefaultUnitW = 52;
 constexpr int strip_width(bool src_z) { return src_z ? 48 : 52; }
 constexpr int kDefaultUnitH = 512;
 constexpr int kNumUnitShapes = 4;
-constexpr int kUnitShapes[kNumUnitShapes][2] = {{52, 256}, {52, 512}, {52, 1024}, {52, 2048}};
+constexpr int kUnitShapes[kNumUnitShapes][2] = {{52, 256}, {52, 512}, {52, 768}, {52, 1024}};
 constexpr int kMaxCtasPerSm = 8;
 constexpr int kWarpsPerCta = 4;
 
