@@ -28,8 +28,9 @@ struct KParams {
   // Largest sum of positive taps over both masks; bounds |L| <= maxval * splus.
   int64_t splus;
   // --- streaming fast path (fx_stream.cuh) ---
-  // Largest input value for which the FP32 evaluation is exact (every LoG
-  // partial sum below 2^24, D below 2^32, t_zc + 1 representable); -1 = never.
+  // Largest input value the first (FP32) pass handles: with the integer masks
+  // every LoG partial sum below 2^24, D below 2^32 and t_zc + 1 representable;
+  // in the FP32-LoG mode D below 2^32 (4095).  -1 = never (all strips redone).
   int32_t fbound;
   // FP32 contrast test: (max - min) - tzc1f < 0  <=>  max - min <= t_zc.
   float tzc1f[2];

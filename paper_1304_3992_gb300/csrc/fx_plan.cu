@@ -1,6 +1,7 @@
-// fx_plan.cu -- plans: the batched persistent kernel over a tile queue (CUDA
-// graph replay), its tile-configuration tuner, the device status word, and the
-// end-to-end entry point on host buffers.
+// fx_plan.cu -- plans: the batched persistent kernels over a tile queue (CUDA
+// graph replay), the per-batch unit height and the tuner, the device status
+// word, and the end-to-end entry points on host buffers (a copy / kernel /
+// copy pipeline over row chunks of one or many images).
 #include <algorithm>
 #include <cstdint>
 #include <cstring>
@@ -495,8 +496,8 @@ fx_status fx_plan_autotune(fx_plan *p, const fx_image_desc *descs, int32_t n, vo
   float best = 1e30f;
   int bw = p->unit_w, bh = p->unit_h, bc = p->ctas_per_sm;
   fx_status st = FX_OK;
-  for (int c = 0; c < kNumUnitShapes && st == FX_OK; ++c) {
-    const int uw = strip_width(p->kp8.source == 1), uh = kUnitShapes[c][1];
+  for (int c = 0; c < kNumUnitHeights && st == FX_OK; ++c) {
+    const int uw = strip_width(p->kp8.source == 1), uh = kUnitHeights[c];
     for (int cps = 1; cps <= kMaxCtasPerSm && st == FX_OK; ++cps) {
       if (!p->fast && uh != kDefaultUnitH) continue;
       if ((st = fx_plan_set_tile(p, uw, uh, cps)) != FX_OK) break;

@@ -1,37 +1,43 @@
 // fx_stream.cuh -- the streaming fast path (device code).
 //
-// One warp computes a strip of 52 output columns over a range of output rows,
-// walking down the image one row per step.  Lane l owns the two adjacent
-// window columns xs + 2l, xs + 2l + 1 of a 64-column window that starts 6
-// columns left of the strip (the halo the stages need: 2 LoG + 1 crossing +
-// 2 median, rounded up to the even column alignment of the loads).  Two
+// One warp computes a strip of 52 output columns (48 with the crossing-map
+// standard deviation) over a range of output rows, walking down the image one
+// row per step.  Lane l owns the two adjacent window columns xs + 2l,
+// xs + 2l + 1 of a 64-column window that starts 6 (8) columns left of the
+// strip: the halo the stages need (2 LoG + 1 crossing (+ 2 deviation) + up to
+// 3 median), rounded up to the even column alignment of the loads.  Two
 // columns per lane keep the per-lane state small, so that several warps per
 // scheduler hide each other's latencies.
 //
 // Per step (one input row t; every value stays in registers):
-//   - one coalesced load of the lane's 2 pixels (plus 2 + 2 halo pixels from
-//     the neighbouring lanes by shuffle);
-//   - horizontal sums h1 = I(x-1) + I(x+1), h2 = I(x-2) + I(x+2) and the
-//     3- and 5-wide sums of squares (integer);
+//   - the lane's two pixels of row t + 4 are loaded into a period-4 ring (one
+//     aligned pair load, or two single-pixel loads), unconditionally; the
+//     replicated border columns are selected when the row is used, and the
+//     +-2-column halo comes from the neighbouring lanes by shuffle;
+//   - horizontal sums h1 = I(x-1) + I(x+1), h2 = I(x-2) + I(x+2) in FP32, and
+//     the 3- and 5-wide sums of squares of the pixels' biased FP32 bits;
 //   - for the centre row c = t-2: the six ring sums R0..R8 of the radial
 //     masks (squared radii 0, 1, 2, 4, 5, 8), L_f = sum_c w_fc R_c for both
-//     masks (Eq. 1, reading R1), and the standard-deviation test of Eq. 2 from
-//     exact sums (reading R4);
+//     masks (Eq. 1, reading R1; FP32-LoG mode: from R_c - n_c I), and the
+//     standard-deviation test of Eq. 2 from exact sums (reading R4);
 //   - for row c' = t-3 (whose four neighbours are now known): the sign of L,
 //     the sign of -L, the signs of the east and south edge sums L(p)+L(q) and
 //     the contrast test (Sec. 3.2), each packed as one bit per pixel.
 // Bits are packed into 32-bit words covering 16 rows x the lane's 2 columns
 // (bit 30 - 2r + j for row r, column j).  Every 16 rows the zero-crossing rule
-// (reading R3), the extraction, the OR of the two maps (Sec. 4.1) and the
-// hybrid median (Sec. 3.4, reading R6) run as bitwise logic on those words,
-// and the finished mask rows are stored.
+// (reading R3), the standard deviation over the crossing map (source 1), the
+// extraction, the OR of the two maps (Sec. 4.1) and one or two hybrid median
+// levels (Sec. 3.4, reading R6) run as bitwise logic on those words, and the
+// finished mask rows are stored.  Each 4-row iteration runs a checked body
+// (border fix-ups, clamped loads) only where the strip touches a border.
 //
-// Arithmetic is exact: the FP32 path is used while every input value is at
-// most KParams::fbound (all LoG partial sums below 2^24, Eq. 2's D below
-// 2^32); a strip that meets a larger value is recomputed on the integer path
-// (int32 LoG, int64 D).  Borders follow reading R2 (every stage replicated):
-// loads clamp, and the L values and mask bits of rows / columns outside the
-// image are replaced by those of the nearest image row / column.
+// Arithmetic is exact with the integer masks: the FP32 path is used while
+// every input value is at most KParams::fbound (all LoG partial sums below
+// 2^24, Eq. 2's D below 2^32); a strip that meets a larger value is
+// recomputed on the integer path (int32 LoG, int64 D).  Borders follow reading
+// R2 (every stage replicated): loads clamp, and the L values and the bits of
+// every binary stage at rows / columns outside the image are replaced by
+// those of the nearest image row / column.
 #pragma once
 #include <cstdint>
 
@@ -39,20 +45,20 @@
 
 namespace fx {
 
-constexpr int kDefaultUnitW = 52;
 // Output columns of a strip: 52, or 48 when the standard deviation is taken
 // over the crossing map (its 5x5 window adds 2 columns to the halo).
 constexpr int strip_width(bool src_z) { return src_z ? 48 : 52; }
 constexpr int kDefaultUnitH = 512;
-constexpr int kNumUnitShapes = 4;
-constexpr int kUnitShapes[kNumUnitShapes][2] = {{52, 256}, {52, 512}, {52, 768}, {52, 1024}};
+// unit heights the batched plan's autotuner times
+constexpr int kNumUnitHeights = 4;
+constexpr int kUnitHeights[kNumUnitHeights] = {256, 512, 768, 1024};
 constexpr int kMaxCtasPerSm = 8;
 constexpr int kWarpsPerCta = 4;
 
 inline bool fast_unit_shape_ok(int w, int h, bool src_z) {
   return w == strip_width(src_z) && h >= 16 && h <= 8192 && h % 16 == 0;
 }
-inline size_t fast_smem_bytes(int, int, int) { return 0; }
+inline size_t fast_smem_bytes(int, int, int) { return 0; }  // static shared memory only
 
 namespace st {
 

@@ -13,8 +13,9 @@
 // This kernel handles every parameter combination (any number of median
 // passes, either standard-deviation source, any dtype) in exact integer
 // arithmetic, or with FP32 responses in the FP32-LoG mode.  The streaming
-// kernel in fx_stream.cu is the fast path for the default configuration;
-// both must agree bit for bit in either mode.
+// kernel in fx_stream.cu is the fast path for every configuration whose median
+// radii add up to at most 3; both must agree bit for bit in either mode (the
+// allocation-free entry point always runs this kernel).
 #include <cstdint>
 
 #pragma once
