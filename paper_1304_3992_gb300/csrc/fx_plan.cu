@@ -297,7 +297,7 @@ fx_status fill_table(fx_plan *p, unsigned char *h, const fx_image_desc *d, int32
     // plus the pipeline overhead, and the batch takes about ceil(units / warps)
     // unit times
     const int64_t slots = static_cast<int64_t>(p->num_sms) * p->ctas_per_sm * kWarpsPerCta;
-    const int64_t overhead = 56 + 16 * ((p->kp8.nhmf == 2 ? 1 : 0) + (p->kp8.source == 1 ? 1 : 0));
+    const int64_t overhead = 20 + p->kp8.r_m + (p->kp8.source == 1 ? 2 : 0);
     int64_t best_cost = INT64_MAX;
     for (int h = 768; h >= 16; h -= 16) {
       int64_t units = 0;

@@ -81,13 +81,14 @@ int64_t warp_slots() {
 }
 
 // Unit height (rows per warp) for an image of `rows` output rows and `units_x`
-// strips: a unit walks uh + overhead rows (ring prefill and pipeline delay), and
-// the launch takes about ceil(units / resident warps) unit times, so small
-// images get short units (parallelism) and large ones long units (less
-// overhead).  Heights are multiples of 16 up to 768.
+// strips: a unit computes about uh + overhead rows (ring prefill, the rows
+// above its first output and the rows below its last one that outputs need),
+// and the launch takes about ceil(units / resident warps) unit times, so small
+// images get short units (parallelism) and large ones long units.  Heights are
+// multiples of 16 up to 768.
 int unit_height(int64_t rows, int64_t units_x, const KParams &kp) {
   const int64_t slots = warp_slots();
-  const int64_t overhead = 56 + 16 * ((kp.nhmf == 2 ? 1 : 0) + (kp.source == 1 ? 1 : 0));
+  const int64_t overhead = 20 + kp.r_m + (kp.source == 1 ? 2 : 0);
   int best = 768;
   int64_t best_cost = INT64_MAX;
   for (int uh = 768; uh >= 16; uh -= 16) {

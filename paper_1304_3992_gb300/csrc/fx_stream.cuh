@@ -792,7 +792,19 @@ struct Strip {
     const int32_t bmax = static_cast<int32_t>((Y1 - Y0 + 2) / 16);
     // one more block of delay per extra median level and for the crossing-map source
     const int32_t iters = 4 * (bmax + (kp.nhmf < 2 ? 3 : 4) + (kSrcZ ? 1 : 0));
+    // the last step whose row feeds an output: the bits of row r are packed at
+    // step r + 3, and the last output row needs the median radius, its south
+    // neighbour (+1) and, for the crossing-map source, the deviation's 2 rows
+    const int32_t t_end = static_cast<int32_t>(Y1 - Y0 - 1) + kp.r_m + 4 + (kSrcZ ? 2 : 0);
     for (int32_t k = -2; k < iters; ++k) {
+      if (4 * k > t_end) {
+        // past the rows any output needs: keep the bit positions of the block
+        // schedule (four steps of two columns) without computing the steps
+#pragma unroll
+        for (int i = 0; i < 12; ++i) acc_[i] <<= 8;
+        if ((k & 3) == 3 && !end_group(k >> 2)) return false;
+        continue;
+      }
       // centre rows of this iteration: 4k - 2 .. 4k + 1 and loaded rows 4k + 4 ..
       // 4k + 7 (relative to Y0); the fix-ups act only on a border strip, at image
       // row 0 and past row H - 1, and loads clamp only outside [rlo, rhi]
