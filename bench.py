@@ -498,7 +498,8 @@ def bench_batched(fx, torch, dev, params, plan_cls):
     plan.close()
     return {"scenes": 64, "pixels": px, "batched_gpx_s": px / t_batch / 1e6,
             "one_by_one_gpx_s": px / t_plain / 1e6, "speedup": t_plain / t_batch,
-            "identical_output": bool(same), "tile": list(tuned)}
+            "identical_output": bool(same),
+            "tile": {"w": tuned[0], "h": tuned[1] or "automatic", "ctas_per_sm": tuned[2]}}
 
 
 def bench_serving(fx, torch, dev, params, master16, duration):

@@ -198,16 +198,18 @@ fx_status fx_extract_batch(fx_plan *plan, const fx_image_desc *descs, int32_t n,
  * strip of tile_w output columns by tile_h output rows walked by one warp;
  * tile_w must be the strip width of the streaming kernel (52, or 48 when the
  * standard deviation is taken over the crossing map) and tile_h a multiple
- * of 16 in [16, 8192]; ctas_per_sm is in 1..8 (4 warps per CTA).
- * Until one of the two calls below fixes the shape, a plan picks the unit
- * height for each batch itself (multiples of 16 up to 768, from the batch's
- * unit count against the resident warps; 3 CTAs per SM).
- * fx_plan_autotune times the heights {256, 512, 768, 1024} x every
- * CTAs-per-SM count the kernel's occupancy allows on the given images (their
- * outputs are overwritten) and keeps the fastest; fx_plan_set_tile forces
- * one.  Plans whose parameters need the general kernel (median windows whose
- * radii add up to more than 3, or more than two levels) use its fixed 64 x 32
- * tile; for them only ctas_per_sm takes effect.
+ * of 16 in [16, 8192], or 0; ctas_per_sm is in 1..8 (4 warps per CTA).
+ * A new plan picks the unit height for each batch itself (multiples of 16 up
+ * to 768, from the batch's unit count against the resident warps; 3 CTAs per
+ * SM) until one of the two calls below fixes another shape.
+ * fx_plan_autotune times the automatic height and the heights
+ * {256, 512, 768, 1024} x every CTAs-per-SM count the kernel's occupancy
+ * allows on the given images (their outputs are overwritten) and keeps the
+ * fastest; fx_plan_set_tile forces one.  In both calls tile_h 0 stands for the
+ * automatic height (picked per batch for the given CTAs per SM).  Plans whose
+ * parameters need the general kernel (median windows whose radii add up to
+ * more than 3, or more than two levels) use its fixed 64 x 32 tile; for them
+ * only ctas_per_sm takes effect.
  * Errors: FX_ERR_INVALID_ARG (shape or count out of range), FX_ERR_CUDA.
  */
 fx_status fx_plan_autotune(fx_plan *plan, const fx_image_desc *descs, int32_t n, void *stream,

@@ -476,14 +476,16 @@ fx_status fx_extract_batch(fx_plan *p, const fx_image_desc *descs, int32_t n, vo
 
 fx_status fx_plan_set_tile(fx_plan *p, int32_t tile_w, int32_t tile_h, int32_t ctas_per_sm) {
   if (!p || ctas_per_sm < 1 || ctas_per_sm > 8) return FX_ERR_INVALID_ARG;
-  if (!fast_unit_shape_ok(tile_w, tile_h, p->kp8.source == 1)) return FX_ERR_INVALID_ARG;
+  // tile_h 0: the height is picked per batch (the wave model in fill_table)
+  const bool automatic = tile_h == 0;
+  if (!fast_unit_shape_ok(tile_w, automatic ? kDefaultUnitH : tile_h, p->kp8.source == 1)) return FX_ERR_INVALID_ARG;
   if (cudaSetDevice(p->device) != cudaSuccess) return FX_ERR_CUDA;
   for (int i = 0; i < 2; ++i)
     if (cudaEventSynchronize(p->h_free[i]) != cudaSuccess) return FX_ERR_CUDA;
   p->unit_w = tile_w;
-  p->unit_h = tile_h;
+  p->unit_h = automatic ? kDefaultUnitH : tile_h;
   p->ctas_per_sm = ctas_per_sm;
-  p->auto_h = false;
+  p->auto_h = automatic;
   return rebuild(p);
 }
 
@@ -496,17 +498,18 @@ fx_status fx_plan_autotune(fx_plan *p, const fx_image_desc *descs, int32_t n, vo
   float best = 1e30f;
   int bw = p->unit_w, bh = p->unit_h, bc = p->ctas_per_sm;
   fx_status st = FX_OK;
-  for (int c = 0; c < kNumUnitHeights && st == FX_OK; ++c) {
-    const int uw = strip_width(p->kp8.source == 1), uh = kUnitHeights[c];
+  // candidates: the automatic height (0), then the fixed heights
+  for (int c = -1; c < kNumUnitHeights && st == FX_OK; ++c) {
+    const int uw = strip_width(p->kp8.source == 1), uh = c < 0 ? 0 : kUnitHeights[c];
     for (int cps = 1; cps <= kMaxCtasPerSm && st == FX_OK; ++cps) {
-      if (!p->fast && uh != kDefaultUnitH) continue;
+      if (!p->fast && uh != 0) continue;
       if ((st = fx_plan_set_tile(p, uw, uh, cps)) != FX_OK) break;
       int occ = 0;
       if (p->fast) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fast_kernel_of(p->kp8, true), 32 * kWarpsPerCta, 0);
       else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batch_kernel_general, 256, p->smem);
       if (occ < cps) continue;
       float t_best = 1e30f;
-      for (int rep = 0; rep < 3 && st == FX_OK; ++rep) {
+      for (int rep = 0; rep < 4 && st == FX_OK; ++rep) {
         cudaEventRecord(e0, s);
         st = fx_extract_batch(p, descs, n, s);
         cudaEventRecord(e1, s);

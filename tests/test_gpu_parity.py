@@ -220,6 +220,25 @@ def test_batch_autotune_keeps_results(cuda_lib):
             assert_same(out.cpu().numpy(), single, f"after autotune {cfg}")
 
 
+def test_batch_set_tile_shapes_keep_results(cuda_lib):
+    """Fixed unit heights (one that splits every image, one taller than all)
+    and the automatic height (tile_h 0) give the same masks."""
+    batch = scenes.uneven_batch(n=5, lo=80, hi=700, seed=9, master_side=800)
+    _, p = pair(16.0)
+    pairs = [(dev_pitched(v, v.strides[0]), torch.zeros(v.shape, dtype=torch.uint8, device="cuda")) for v, _ in batch]
+    singles = [run(cuda_lib, img, p) for img, _ in pairs]
+    with cuda_lib.Plan(p, max_images=8) as plan:
+        for shape in [(52, 16, 1), (52, 1024, 2), (52, 0, 3), (52, 0, 1)]:
+            plan.set_tile(*shape)
+            for o in pairs:
+                o[1].fill_(9)
+            plan.extract_batch(pairs)
+            torch.cuda.synchronize()
+            for (img, out), single in zip(pairs, singles):
+                assert_same(out.cpu().numpy(), single, f"tile {shape}")
+        assert plan.device_status() == 0
+
+
 def test_extract_host_matches_device(cuda_lib):
     img = scenes.scene(1500, 1300, seed=31, n_rects=200, noise_sigma=24, impulse_frac=0.005, bits=12)
     _, p = pair(16.0)
