@@ -26,11 +26,16 @@ struct BatchImage {
   int32_t pad;
 };
 
+// Streaming path: the queue holds four groups of images, in this order: read
+// with one aligned load per lane (uint16, uint8), then pixel by pixel (uint16,
+// uint8).  Group g owns the units [group_end[g-1], group_end[g]) (group_end[-1]
+// = 0) and runs in a kernel of its own.
+constexpr int kGroups = 4;
+__host__ __device__ constexpr int group_of(bool pair, int elem) { return (pair ? 0 : 2) + (elem == 1 ? 1 : 0); }
+
 struct BatchHeader {
   int64_t total_units;
-  // streaming path: units [0, pair_units) belong to images read with one aligned
-  // load per lane (listed first), the rest to images read pixel by pixel
-  int64_t pair_units;
+  int64_t group_end[kGroups];  // streaming path only
   int32_t n;
   int32_t unit_w, unit_h;  // unit shape in output pixels
   int32_t pad;
@@ -88,37 +93,35 @@ __global__ void __launch_bounds__(256) batch_kernel_general(const unsigned char 
   }
 }
 
-// kPair: the units [0, pair_units) from counter[0]; otherwise [pair_units,
-// total_units) from counter[1].  The two run as consecutive launches, so each
-// kernel holds one strip loop per dtype.
-template <bool kF32Log, bool kPair, bool kSd2, bool kSrcZ>
+// One group of the streaming path (load path kPair, pixel type T): its units
+// from counter[g].  Each group is a kernel of its own, so a kernel holds one
+// strip loop (the register allocation and instruction working set of the
+// single-image kernel).
+template <typename T, bool kF32Log, bool kPair, bool kSd2, bool kSrcZ>
 __global__ void __launch_bounds__(32 * kWarpsPerCta, 3) batch_kernel_fast(const unsigned char *table,
                                                                       unsigned long long *counter, int *status,
-                                                                      const __grid_constant__ KParams kp8,
-                                                                      const __grid_constant__ KParams kp16) {
+                                                                      const __grid_constant__ KParams kp) {
   __shared__ StripWords words;
+  constexpr int g = group_of(kPair, sizeof(T));
   const BatchHeader *hdr = reinterpret_cast<const BatchHeader *>(table);
   const BatchImage *ims = reinterpret_cast<const BatchImage *>(table + sizeof(BatchHeader));
-  const long long first = kPair ? 0 : hdr->pair_units;
-  const long long end = kPair ? hdr->pair_units : hdr->total_units;
+  const long long first = g == 0 ? 0 : hdr->group_end[g - 1];
+  const long long end = hdr->group_end[g];
   const int lane = threadIdx.x & 31;
   for (;;) {
     unsigned long long got = 0;
-    if (lane == 0) got = atomicAdd(counter + (kPair ? 0 : 1), 1ULL);
+    if (lane == 0) got = atomicAdd(counter + g, 1ULL);
     const long long u = first + static_cast<long long>(__shfl_sync(0xffffffffu, got, 0));
     if (u >= end) break;
     const BatchImage &b = ims[find_image(ims, hdr->n, u)];
-    if (b.units_x <= 0 || (b.elem != 1 && b.elem != 2)) {
+    if (b.units_x <= 0 || b.elem != static_cast<int32_t>(sizeof(T))) {
       if (lane == 0) atomicOr(status, kStatusBadDescriptor);
       continue;
     }
     const ImageView v = view_of(b);
     const long long local = u - b.unit_begin;
     const int64_t ux = local % b.units_x, uy = local / b.units_x;
-    if (b.elem == 1)
-      fast_unit<uint8_t, kF32Log, kPair, kSd2, kSrcZ>(v, kp8, ux, uy, hdr->unit_w, hdr->unit_h, warp_words(words));
-    else
-      fast_unit<uint16_t, kF32Log, kPair, kSd2, kSrcZ>(v, kp16, ux, uy, hdr->unit_w, hdr->unit_h, warp_words(words));
+    fast_unit<T, kF32Log, kPair, kSd2, kSrcZ>(v, kp, ux, uy, hdr->unit_w, hdr->unit_h, warp_words(words));
   }
 }
 
@@ -150,17 +153,25 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta, 3) batch_kernel_redo(const 
   }
 }
 
-// The streaming kernels of a plan's parameters (LoG mode, load path,
+// The streaming kernel of group g for a plan's parameters (LoG mode,
 // standard-deviation source and thresholds).
-template <bool kF32Log, bool kPair>
+template <typename T, bool kF32Log, bool kPair>
 const void *fast_kernel_sd(const KParams &kp) {
-  if (kp.source == 1) return reinterpret_cast<const void *>(&batch_kernel_fast<kF32Log, kPair, false, true>);
-  return kp.sd_same ? reinterpret_cast<const void *>(&batch_kernel_fast<kF32Log, kPair, false, false>)
-                    : reinterpret_cast<const void *>(&batch_kernel_fast<kF32Log, kPair, true, false>);
+  if (kp.source == 1) return reinterpret_cast<const void *>(&batch_kernel_fast<T, kF32Log, kPair, false, true>);
+  return kp.sd_same ? reinterpret_cast<const void *>(&batch_kernel_fast<T, kF32Log, kPair, false, false>)
+                    : reinterpret_cast<const void *>(&batch_kernel_fast<T, kF32Log, kPair, true, false>);
 }
-const void *fast_kernel_of(const KParams &kp, bool pair) {
-  if (kp.f32log) return pair ? fast_kernel_sd<true, true>(kp) : fast_kernel_sd<true, false>(kp);
-  return pair ? fast_kernel_sd<false, true>(kp) : fast_kernel_sd<false, false>(kp);
+template <bool kF32Log>
+const void *fast_kernel_mode(const KParams &kp, int g) {
+  switch (g) {
+    case 0: return fast_kernel_sd<uint16_t, kF32Log, true>(kp);
+    case 1: return fast_kernel_sd<uint8_t, kF32Log, true>(kp);
+    case 2: return fast_kernel_sd<uint16_t, kF32Log, false>(kp);
+    default: return fast_kernel_sd<uint8_t, kF32Log, false>(kp);
+  }
+}
+const void *fast_kernel_of(const KParams &kp, int g) {
+  return kp.f32log ? fast_kernel_mode<true>(kp, g) : fast_kernel_mode<false>(kp, g);
 }
 template <bool kF32Log>
 const void *redo_kernel_src(const KParams &kp) {
@@ -221,11 +232,14 @@ size_t unit_smem(const fx_plan *p) {
   return std::max(gen::general_smem_bytes(p->kp8), gen::general_smem_bytes(p->kp16));
 }
 
-// Graph i: copy host table i to the device, zero the queue counter, run the
-// persistent kernel.  The table copy has a fixed size so the graph never changes.
+// Graph i: copy host table i to the device, zero the queue counters, run the
+// persistent kernel (general path), or the four group kernels of the streaming
+// path as independent nodes (a group's CTAs take the SMs that the previous
+// group's drained queue frees) followed by the redo pass.  The table copy has
+// a fixed size so the graph never changes.
 fx_status build_graph(fx_plan *p, int i) {
   p->smem = unit_smem(p);
-  const void *fn = p->fast ? fast_kernel_of(p->kp8, true) : reinterpret_cast<const void *>(&batch_kernel_general);
+  const void *fn = p->fast ? fast_kernel_of(p->kp8, 0) : reinterpret_cast<const void *>(&batch_kernel_general);
   if (!p->fast &&  // the streaming kernels use static shared memory only
       cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) != cudaSuccess)
     return FX_ERR_CUDA;
@@ -243,9 +257,9 @@ fx_status build_graph(fx_plan *p, int i) {
   ms.dst = p->d_counter;
   ms.value = 0;
   ms.elementSize = 4;
-  ms.width = 4;  // both queue counters
+  ms.width = 2 * kGroups;  // the queue counters
   ms.height = 1;
-  ms.pitch = 16;
+  ms.pitch = 8 * kGroups;
   const unsigned char *tab = p->d_table;
   unsigned long long *ctr = p->d_counter;
   int *stp = p->d_status;
@@ -260,18 +274,23 @@ fx_status build_graph(fx_plan *p, int i) {
   kn.kernelParams = args;
   cudaError_t e = cudaGraphAddMemcpyNode(&n_copy, g, nullptr, 0, &cp);
   if (e == cudaSuccess) e = cudaGraphAddMemsetNode(&n_zero, g, &n_copy, 1, &ms);
-  if (e == cudaSuccess) e = cudaGraphAddKernelNode(&n_kern, g, &n_zero, 1, &kn);
-  if (e == cudaSuccess && p->fast) {
-    // images read pixel by pixel, then the integer (or wide) redo pass
-    cudaKernelNodeParams kb = kn;
-    kb.func = const_cast<void *>(fast_kernel_of(p->kp8, false));
-    cudaGraphNode_t n_kb;
-    e = cudaGraphAddKernelNode(&n_kb, g, &n_kern, 1, &kb);
+  if (!p->fast) {
+    if (e == cudaSuccess) e = cudaGraphAddKernelNode(&n_kern, g, &n_zero, 1, &kn);
+  } else {
+    cudaGraphNode_t n_grp[kGroups];
+    for (int gi = 0; gi < kGroups && e == cudaSuccess; ++gi) {
+      KParams *kg = gi % 2 == 1 ? &k8 : &k16;  // groups 1 and 3 hold the uint8 images
+      void *gargs[] = {&tab, &ctr, &stp, kg};
+      cudaKernelNodeParams kf = kn;
+      kf.func = const_cast<void *>(fast_kernel_of(p->kp8, gi));
+      kf.kernelParams = gargs;
+      e = cudaGraphAddKernelNode(&n_grp[gi], g, &n_zero, 1, &kf);
+    }
+    // the integer (or wide) redo pass after all groups
     cudaKernelNodeParams kr = kn;
     kr.func = const_cast<void *>(redo_kernel_of(p->kp8));
     kr.sharedMemBytes = 0;
-    cudaGraphNode_t n_redo;
-    if (e == cudaSuccess) e = cudaGraphAddKernelNode(&n_redo, g, &n_kb, 1, &kr);
+    if (e == cudaSuccess) e = cudaGraphAddKernelNode(&n_kern, g, n_grp, kGroups, &kr);
   }
   if (e == cudaSuccess) e = cudaGraphInstantiate(&p->graph[i], g, 0);
   cudaGraphDestroy(g);
@@ -311,12 +330,10 @@ fx_status fill_table(fx_plan *p, unsigned char *h, const fx_image_desc *d, int32
     }
   }
   const int uw = p->fast ? p->unit_w : gen::TW;
-  int64_t total = 0, pair_units = 0;
-  // On the streaming path the queue runs through the images in four groups:
-  // one aligned load per lane (uint16, then uint8), then pixel by pixel (uint16,
-  // then uint8).  The first two groups go to one kernel and the last two to
-  // the next, and within a kernel the warps of an SM mostly run the loop of
-  // one dtype at a time, which keeps the instruction working set small.
+  int64_t total = 0, group_end[kGroups] = {0, 0, 0, 0};
+  // On the streaming path the queue runs through the images in four groups
+  // (group_of): one aligned load per lane (uint16, then uint8), then pixel by
+  // pixel (uint16, then uint8); each group is one kernel with one strip loop.
   int32_t slot = 0;
   for (int pass = 0; pass < (p->fast ? 4 : 1); ++pass)
   for (int32_t i = 0; i < n; ++i) {
@@ -324,7 +341,7 @@ fx_status fill_table(fx_plan *p, unsigned char *h, const fx_image_desc *d, int32
     const int64_t elem = d[i].dtype == FX_U8 ? 1 : 2;
     const bool pair = p->fast && reinterpret_cast<uintptr_t>(d[i].img) % (2 * elem) == 0 &&
                       d[i].pitch_bytes % (2 * elem) == 0 && d[i].width % 2 == 0;
-    if (p->fast && (pair != (pass < 2) || (d[i].dtype == FX_U8) != (pass % 2 == 1))) continue;
+    if (p->fast && group_of(pair, static_cast<int>(elem)) != pass) continue;
     fx_status st = check_image(d[i].img, d[i].width, d[i].height, d[i].pitch_bytes, d[i].dtype,
                                d[i].out_mask, op);
     if (st != FX_OK) return st;
@@ -341,7 +358,7 @@ fx_status fill_table(fx_plan *p, unsigned char *h, const fx_image_desc *d, int32
     b.units_x = (b.width + uwx - 1) / uwx;
     b.unit_begin = total;
     total += b.units_x * ((b.height + uh - 1) / uh);
-    if (pass < 2) pair_units = total;
+    if (p->fast) group_end[pass] = total;
   }
   if (slot != n) return FX_ERR_INVALID_ARG;  // every descriptor belongs to exactly one group
   // outputs must not overlap each other (inputs were checked per descriptor)
@@ -354,7 +371,10 @@ fx_status fill_table(fx_plan *p, unsigned char *h, const fx_image_desc *d, int32
       if ((a0 < b1 && b0 < a1) || (a0 < c1 && c0 < a1) || (b0 < e1 && e0 < b1)) return FX_ERR_INVALID_ARG;
     }
   hdr->total_units = total;
-  hdr->pair_units = p->fast ? pair_units : total;
+  for (int gi = 0; gi < kGroups; ++gi) {  // a group with no image ends where the previous one does
+    if (gi > 0) group_end[gi] = std::max(group_end[gi], group_end[gi - 1]);
+    hdr->group_end[gi] = p->fast ? group_end[gi] : total;
+  }
   hdr->n = n;
   hdr->unit_w = uw;
   hdr->unit_h = uh;
@@ -408,7 +428,7 @@ fx_status fx_plan_create(fx_plan **out, const fx_params *params, int32_t max_ima
     return FX_ERR_CUDA;
   }
   bool ok = cudaMalloc(&p->d_table, table_bytes(max_images)) == cudaSuccess &&
-            cudaMalloc(&p->d_counter, 16) == cudaSuccess && cudaMalloc(&p->d_status, 4) == cudaSuccess &&
+            cudaMalloc(&p->d_counter, 8 * kGroups) == cudaSuccess && cudaMalloc(&p->d_status, 4) == cudaSuccess &&
             cudaMemset(p->d_status, 0, 4) == cudaSuccess;
   for (int i = 0; i < 2 && ok; ++i) {
     ok = cudaMallocHost(&p->h_table[i], table_bytes(max_images)) == cudaSuccess &&
@@ -505,7 +525,7 @@ fx_status fx_plan_autotune(fx_plan *p, const fx_image_desc *descs, int32_t n, vo
       if (!p->fast && uh != 0) continue;
       if ((st = fx_plan_set_tile(p, uw, uh, cps)) != FX_OK) break;
       int occ = 0;
-      if (p->fast) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fast_kernel_of(p->kp8, true), 32 * kWarpsPerCta, 0);
+      if (p->fast) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fast_kernel_of(p->kp8, 0), 32 * kWarpsPerCta, 0);
       else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batch_kernel_general, 256, p->smem);
       if (occ < cps) continue;
       float t_best = 1e30f;
