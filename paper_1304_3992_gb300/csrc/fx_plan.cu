@@ -127,9 +127,11 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta, 3) batch_kernel_fast(const 
 
 // Second pass of the streaming path: every warp walks the units with a static
 // stride and recomputes, on the integer (or wide FP32-LoG) path, the strips
-// the first pass marked.
+// the first pass marked.  2 CTAs per SM (no spill of the 64-bit sums); the
+// graph launches exactly the resident CTAs, so no CTA waits for a second wave
+// with its share of the stride.
 template <bool kF32Log, bool kSrcZ>
-__global__ void __launch_bounds__(32 * kWarpsPerCta, 3) batch_kernel_redo(const unsigned char *table,
+__global__ void __launch_bounds__(32 * kWarpsPerCta, 2) batch_kernel_redo(const unsigned char *table,
                                                                       unsigned long long *, int *,
                                                                       const __grid_constant__ KParams kp8,
                                                                       const __grid_constant__ KParams kp16) {
@@ -286,10 +288,13 @@ fx_status build_graph(fx_plan *p, int i) {
       kf.kernelParams = gargs;
       e = cudaGraphAddKernelNode(&n_grp[gi], g, &n_zero, 1, &kf);
     }
-    // the integer (or wide) redo pass after all groups
+    // the integer (or wide) redo pass after all groups, one wave of CTAs
     cudaKernelNodeParams kr = kn;
     kr.func = const_cast<void *>(redo_kernel_of(p->kp8));
     kr.sharedMemBytes = 0;
+    int occ = 0;
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kr.func, 32 * kWarpsPerCta, 0);
+    kr.gridDim = dim3(static_cast<unsigned>(p->num_sms * std::max(1, occ)));
     if (e == cudaSuccess) e = cudaGraphAddKernelNode(&n_kern, g, n_grp, kGroups, &kr);
   }
   if (e == cudaSuccess) e = cudaGraphInstantiate(&p->graph[i], g, 0);
