@@ -307,7 +307,7 @@ def main():
     # ---- parameter variants and the grayscale median op on band 0
     variants = None
     if not args.no_variants:
-        variants = bench_variants(fx, torch, stream, bands[0], outs[0])
+        variants = bench_variants(fx, torch, stream, bands[0], outs[0], bands_np[0])
 
     # ---- end to end through the C ABI on pinned host buffers
     h_in = [torch.from_numpy(b).pin_memory() for b in bands_np]
@@ -421,9 +421,11 @@ def bench_fp32_log(fx, torch, stream, bands, outs_int, warmup, steps):
             "launch": "fx_extract per band, log_mode FX_LOG_FP32 (FP32 pass + wide-pass marker check)"}
 
 
-def bench_variants(fx, torch, stream, band, out, reps=5):
+def bench_variants(fx, torch, stream, band, out, band_np, reps=5):
     """Throughput of fx_extract on one band for the parameter variants (which
-    kernel runs them is recorded), and of the grayscale hybrid median op."""
+    kernel runs them is recorded), on the same band scaled to the full 16-bit
+    range (above the FP32-exact bound: the integer pass computes it), and of
+    the grayscale hybrid median op."""
     base = dict(sigma=(0.5, 20.0), mask_q=512)
     cases = {
         "median_off": (dict(hmf=()), "streaming"),
@@ -455,6 +457,12 @@ def bench_variants(fx, torch, stream, band, out, reps=5):
         p = fx.make_params(fx.FX_U16, 12, **kw)
         ms = timed(lambda: fx.extract(band, p, out=out, stream=stream))
         res[name] = {"gpx_s": px / ms / 1e6, "ms": ms, "kernel": kernel}
+    wide = torch.from_numpy(band_np * np.uint16(16)).to(band.device)  # values up to 65520
+    p16 = fx.make_params(fx.FX_U16, 16)
+    ms = timed(lambda: fx.extract(wide, p16, out=out, stream=stream))
+    res["full_range_16bit"] = {"gpx_s": px / ms / 1e6, "ms": ms,
+                               "kernel": "streaming first pass (stops at the first block) + integer pass"}
+    del wide
     med = torch.empty_like(band)
     for w in (3, 5):
         ms = timed(lambda: fx.hybrid_median(band, w, out=med, stream=stream))
