@@ -200,8 +200,8 @@ fx_status fx_extract_batch(fx_plan *plan, const fx_image_desc *descs, int32_t n,
  * standard deviation is taken over the crossing map) and tile_h a multiple
  * of 16 in [16, 8192], or 0; ctas_per_sm is in 1..8 (4 warps per CTA).
  * A new plan picks the unit height for each batch itself (multiples of 16 up
- * to 768, from the batch's unit count against the resident warps; 3 CTAs per
- * SM) until one of the two calls below fixes another shape.
+ * to 1024, from the batch's unit count against the resident warps; 3 CTAs
+ * per SM) until one of the two calls below fixes another shape.
  * fx_plan_autotune times the automatic height and the heights
  * {256, 512, 768, 1024} x every CTAs-per-SM count the kernel's occupancy
  * allows on the given images (their outputs are overwritten) and keeps the

@@ -121,7 +121,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta, 3) batch_kernel_fast(const 
     const ImageView v = view_of(b);
     const long long local = u - b.unit_begin;
     const int64_t ux = local % b.units_x, uy = local / b.units_x;
-    fast_unit<T, kF32Log, kPair, kSd2, kSrcZ>(v, kp, ux, uy, hdr->unit_w, hdr->unit_h, warp_words(words));
+    fast_unit<T, kF32Log, kPair, kSd2, kSrcZ, false>(v, kp, ux, uy, hdr->unit_w, hdr->unit_h, warp_words(words));
   }
 }
 
@@ -318,12 +318,13 @@ fx_status fill_table(fx_plan *p, unsigned char *h, const fx_image_desc *d, int32
   int uh = p->fast ? p->unit_h : gen::TH;
   if (p->fast && p->auto_h) {
     // the wave model of fx_extract over the whole batch: a warp walks uh rows
-    // plus the pipeline overhead, and the batch takes about ceil(units / warps)
-    // unit times
+    // plus the pipeline overhead (the batched units run the whole block
+    // schedule: ring prefill and three to five blocks of delay), and the batch
+    // takes about ceil(units / warps) unit times
     const int64_t slots = static_cast<int64_t>(p->num_sms) * p->ctas_per_sm * kWarpsPerCta;
-    const int64_t overhead = 20 + p->kp8.r_m + (p->kp8.source == 1 ? 2 : 0);
+    const int64_t overhead = 56 + 16 * ((p->kp8.nhmf == 2 ? 1 : 0) + (p->kp8.source == 1 ? 1 : 0));
     int64_t best_cost = INT64_MAX;
-    for (int h = 768; h >= 16; h -= 16) {
+    for (int h = 1024; h >= 16; h -= 16) {
       int64_t units = 0;
       for (int32_t i = 0; i < n; ++i)
         units += std::max<int64_t>(1, (d[i].width + uwx - 1) / uwx) * std::max<int64_t>(1, (d[i].height + h - 1) / h);

@@ -780,6 +780,9 @@ struct Strip {
     step<3, kChk>(t0 + 3);
   }
 
+  // kTail: skip the steps past the last row any output needs (single-image
+  // launches; the batched kernels, whose units are long, run without it).
+  template <bool kTail = true>
   __device__ bool run() {
     // Rows Y0-8 .. Y0-1 (k = -2, -1) fill the rings; they compute responses and
     // bits of rows no output depends on.  Bit blocks span 16 rows (four
@@ -795,15 +798,17 @@ struct Strip {
     // the last step whose row feeds an output: the bits of row r are packed at
     // step r + 3, and the last output row needs the median radius, its south
     // neighbour (+1) and, for the crossing-map source, the deviation's 2 rows
-    const int32_t t_end = static_cast<int32_t>(Y1 - Y0 - 1) + kp.r_m + 4 + (kSrcZ ? 2 : 0);
+    [[maybe_unused]] const int32_t t_end = static_cast<int32_t>(Y1 - Y0 - 1) + kp.r_m + 4 + (kSrcZ ? 2 : 0);
     for (int32_t k = -2; k < iters; ++k) {
-      if (4 * k > t_end) {
-        // past the rows any output needs: keep the bit positions of the block
-        // schedule (four steps of two columns) without computing the steps
+      if constexpr (kTail) {
+        if (4 * k > t_end) {
+          // past the rows any output needs: keep the bit positions of the block
+          // schedule (four steps of two columns) without computing the steps
 #pragma unroll
-        for (int i = 0; i < 12; ++i) acc_[i] <<= 8;
-        if ((k & 3) == 3 && !end_group(k >> 2)) return false;
-        continue;
+          for (int i = 0; i < 12; ++i) acc_[i] <<= 8;
+          if ((k & 3) == 3 && !end_group(k >> 2)) return false;
+          continue;
+        }
       }
       // centre rows of this iteration: 4k - 2 .. 4k + 1 and loaded rows 4k + 4 ..
       // 4k + 7 (relative to Y0); the fix-ups act only on a border strip, at image
@@ -845,7 +850,7 @@ __device__ __forceinline__ uint32_t (*warp_words(StripWords &w))[32] { return w[
 // kF32Log selects the FP32-LoG mode (KParams::f32log) at compile time; kSd2 =
 // !KParams::sd_same (kSd2 = true is correct for any thresholds); kSrcZ =
 // (KParams::source == 1).
-template <typename T, bool kF32Log, bool kPair, bool kSd2, bool kSrcZ>
+template <typename T, bool kF32Log, bool kPair, bool kSd2, bool kSrcZ, bool kTail = true>
 __device__ __forceinline__ void fast_unit(const ImageView &v, const KParams &kp, int64_t ux, int64_t uy, int,
                                           int uh, uint32_t (*words)[32]) {
   constexpr int kMode = kF32Log ? st::kModeF32Log : st::kModeF32;
@@ -856,7 +861,7 @@ __device__ __forceinline__ void fast_unit(const ImageView &v, const KParams &kp,
   const int64_t Y0 = v.y_begin + uy * uh;
   const int64_t Y1 = Y0 + uh < v.y_end ? Y0 + uh : v.y_end;
   st::Strip<T, kMode, kPair, kSd2, kSrcZ> s(v, kp, X0, Y0, Y1, words);
-  if (!s.run() && (threadIdx.x & 31) == 0) *unit_marker(v, ux, uy, uh, uw) = kRedo;
+  if (!s.template run<kTail>() && (threadIdx.x & 31) == 0) *unit_marker(v, ux, uy, uh, uw) = kRedo;
 }
 
 template <typename T, bool kF32Log, bool kSrcZ>
