@@ -16,7 +16,10 @@
 // handles two pixels.  A ring of k rows keeps, per row, the words of the
 // lane's pixels shifted by -2..2 columns (neighbour lanes by shuffle, one-
 // column shifts by byte selection); loads are issued k rows ahead into a ring
-// of their own and never sit inside a branch.
+// of their own and never sit inside a branch.  For uint16 images read as
+// aligned pairs the loads go instead through a per-warp shared-memory ring of
+// kAsyncRows rows filled by cp.async, kAsyncRows - 1 rows ahead: many more
+// bytes in flight per SM than a register ring allows, at no register cost.
 #include <cstdint>
 #include <utility>
 
@@ -28,7 +31,17 @@ namespace {
 constexpr int kHmfOut = 60;    // output columns per strip (lanes 1..30)
 constexpr int kHmfUnitH = 256; // output rows per strip unit
 constexpr int kHmfWarps = 4;   // warps per CTA
+constexpr int kAsyncRows = 16; // depth of the shared-memory load ring (power of two)
 constexpr unsigned kAll = 0xffffffffu;
+
+// 4-byte asynchronous copy global -> shared (the thread's own group queue)
+__device__ __forceinline__ void cp_async4(uint32_t *dst, const void *src) {
+  const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst));
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
 __device__ __forceinline__ uint32_t vmin(uint32_t a, uint32_t b) {
   uint32_t d;
@@ -71,6 +84,9 @@ template <typename T, int K, bool kPair>
 struct HmfStrip {
   static constexpr int R = K / 2;
   static constexpr int L = K;  // loads run one window (k rows) ahead
+  // aligned uint16 pairs: 4-byte asynchronous copies into the warp's ring
+  static constexpr bool kAsync = kPair && sizeof(T) == 2;
+  uint32_t (*ring_)[32] = nullptr;  // kAsyncRows x 32 words of this warp (kAsync)
   const unsigned char *p0_, *p1_;  // this lane's load addresses in image row 0
   uint32_t sel_;
   int64_t pitch, H, Y0, Y1, W, x;
@@ -100,6 +116,15 @@ struct HmfStrip {
     }
   }
 
+  // kAsync: input row Y0 - R + t (clamped) into ring slot t mod kAsyncRows, as
+  // one commit group
+  __device__ __forceinline__ void issue(int64_t t) {
+    int64_t y = Y0 - R + t;
+    y = y < 0 ? 0 : (y >= H ? H - 1 : y);
+    cp_async4(&ring_[t & (kAsyncRows - 1)][lane], p0_ + y * pitch);
+    cp_async_commit();
+  }
+
   // input row Y0 - R + t (clamped to the image) into load slot S
   template <int S>
   __device__ __forceinline__ void load(int64_t t) {
@@ -118,9 +143,17 @@ struct HmfStrip {
   __device__ __forceinline__ void step(int64_t t) {  // SL = t % L; window slot S = t % K
     constexpr int S = SL % K;
     // (column 2l, 2l+1) as a u16x2 word; the selection also copies the slot before it is refilled
-    const uint32_t w = kPair ? __byte_perm(raw0_[SL], 0, sel_) : __byte_perm(raw0_[SL], raw1_[SL], 0x5410);
-    load<SL>(t + L);
+    uint32_t w;
+    if constexpr (kAsync) {
+      cp_async_wait<kAsyncRows - 2>();  // row t has landed (rows t + 1 .. t + kAsyncRows - 2 may be in flight)
+      w = __byte_perm(ring_[t & (kAsyncRows - 1)][lane], 0, sel_);
+    } else {
+      w = kPair ? __byte_perm(raw0_[SL], 0, sel_) : __byte_perm(raw0_[SL], raw1_[SL], 0x5410);
+      load<SL>(t + L);
+    }
     const uint32_t pv = __shfl_up_sync(kAll, w, 1), nx = __shfl_down_sync(kAll, w, 1);
+    // refill the slot of row t - 1, whose value the previous step has used
+    if constexpr (kAsync) issue(t + kAsyncRows - 1);
     win_[S][0] = pv;                         // columns -2, -1
     win_[S][1] = __byte_perm(pv, w, 0x5432); // -1, 0
     win_[S][2] = w;
@@ -159,9 +192,14 @@ struct HmfStrip {
   }
 
   __device__ void run() {
-    loads(std::make_integer_sequence<int, L>{});
+    if constexpr (kAsync) {
+      for (int t = 0; t < kAsyncRows - 1; ++t) issue(t);
+    } else {
+      loads(std::make_integer_sequence<int, L>{});
+    }
     const int64_t last = Y1 - Y0 + 2 * R;  // steps 0 .. last - 1 cover output rows Y0 .. Y1 - 1
     for (int64_t t0 = 0; t0 < last; t0 += L) steps(t0, std::make_integer_sequence<int, L>{});
+    if constexpr (kAsync) cp_async_wait<0>();  // no copy outlives the warp
   }
 };
 
@@ -174,6 +212,10 @@ __global__ void __launch_bounds__(32 * kHmfWarps) hmf_stream_kernel(const T *img
   const int64_t ux = unit % units_x, uy = unit / units_x;
   const int64_t Y0 = uy * kHmfUnitH, Y1 = Y0 + kHmfUnitH < H ? Y0 + kHmfUnitH : H;
   HmfStrip<T, K, kPair> s(img, W, H, pitch, out, out_pitch, ux * kHmfOut, Y0, Y1);
+  if constexpr (HmfStrip<T, K, kPair>::kAsync) {
+    __shared__ uint32_t ring[kHmfWarps][kAsyncRows][32];
+    s.ring_ = ring[threadIdx.x >> 5];
+  }
   s.run();
 }
 
