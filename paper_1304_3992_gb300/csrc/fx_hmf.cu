@@ -93,6 +93,14 @@ struct HmfStrip {
   unsigned char *out_;
   int64_t opitch;
   int lane;
+  // 32-bit row arithmetic: step t reads input row Y0 - R + clamp(t, tlo_, thi_)
+  // at q0_ / q1_ + (clamped t - tb_) * pitch, and writes output row Y0 + t - 2R
+  // (when in [0, nrows_)) at outb_ + (t - 2R) * opitch
+  int32_t tlo_, thi_, tb_, nrows_;
+  const unsigned char *q0_, *q1_;
+  unsigned char *outb_;
+  uint32_t pitch32_, opitch32_;
+  bool vst_;  // one store of the lane's two output pixels (aligned rows)
   uint32_t raw0_[L], raw1_[L];  // loaded pixels of the next L rows
   uint32_t win_[K][5];          // per ring row: the pair words shifted by -2..2 columns
 
@@ -114,33 +122,47 @@ struct HmfStrip {
       p1_ = reinterpret_cast<const unsigned char *>(img) + c1 * static_cast<int64_t>(sizeof(T));
       sel_ = 0x5410u;
     }
+    // pitches are below 2^32 bytes and sides below 2^30 (checked by the host)
+    tlo_ = static_cast<int32_t>(R - Y0);
+    thi_ = static_cast<int32_t>(H - 1 - Y0 + R);
+    tb_ = tlo_ > 0 ? tlo_ : 0;
+    q0_ = p0_ + (Y0 - R + tb_) * pitch;
+    q1_ = p1_ + (Y0 - R + tb_) * pitch;
+    pitch32_ = static_cast<uint32_t>(pitch);
+    opitch32_ = static_cast<uint32_t>(opitch);
+    nrows_ = static_cast<int32_t>(Y1 - Y0);
+    outb_ = out_ + Y0 * opitch + x * static_cast<int64_t>(sizeof(T));
+    vst_ = reinterpret_cast<uintptr_t>(out_) % (2 * sizeof(T)) == 0 && opitch % (2 * sizeof(T)) == 0;
+  }
+
+  // byte offset of the input row that step t reads (clamped to the image)
+  __device__ __forceinline__ uint64_t row_off(int32_t t) const {
+    const int32_t tc = t < tlo_ ? tlo_ : (t > thi_ ? thi_ : t);
+    return static_cast<uint64_t>(static_cast<uint32_t>(tc - tb_)) * pitch32_;
   }
 
   // kAsync: input row Y0 - R + t (clamped) into ring slot t mod kAsyncRows, as
   // one commit group
-  __device__ __forceinline__ void issue(int64_t t) {
-    int64_t y = Y0 - R + t;
-    y = y < 0 ? 0 : (y >= H ? H - 1 : y);
-    cp_async4(&ring_[t & (kAsyncRows - 1)][lane], p0_ + y * pitch);
+  __device__ __forceinline__ void issue(int32_t t) {
+    cp_async4(&ring_[t & (kAsyncRows - 1)][lane], q0_ + row_off(t));
     cp_async_commit();
   }
 
   // input row Y0 - R + t (clamped to the image) into load slot S
   template <int S>
-  __device__ __forceinline__ void load(int64_t t) {
-    int64_t y = Y0 - R + t;
-    y = y < 0 ? 0 : (y >= H ? H - 1 : y);
+  __device__ __forceinline__ void load(int32_t t) {
+    const uint64_t off = row_off(t);
     if constexpr (kPair) {
-      if constexpr (sizeof(T) == 2) raw0_[S] = __ldg(reinterpret_cast<const uint32_t *>(p0_ + y * pitch));
-      else raw0_[S] = __ldg(reinterpret_cast<const uint16_t *>(p0_ + y * pitch));
+      if constexpr (sizeof(T) == 2) raw0_[S] = __ldg(reinterpret_cast<const uint32_t *>(q0_ + off));
+      else raw0_[S] = __ldg(reinterpret_cast<const uint16_t *>(q0_ + off));
     } else {
-      raw0_[S] = __ldg(reinterpret_cast<const T *>(p0_ + y * pitch));
-      raw1_[S] = __ldg(reinterpret_cast<const T *>(p1_ + y * pitch));
+      raw0_[S] = __ldg(reinterpret_cast<const T *>(q0_ + off));
+      raw1_[S] = __ldg(reinterpret_cast<const T *>(q1_ + off));
     }
   }
 
   template <int SL>
-  __device__ __forceinline__ void step(int64_t t) {  // SL = t % L; window slot S = t % K
+  __device__ __forceinline__ void step(int32_t t) {  // SL = t % L; window slot S = t % K
     constexpr int S = SL % K;
     // (column 2l, 2l+1) as a u16x2 word; the selection also copies the slot before it is refilled
     uint32_t w;
@@ -160,8 +182,8 @@ struct HmfStrip {
     win_[S][3] = __byte_perm(w, nx, 0x5432); //  1, 2
     win_[S][4] = nx;                         //  2, 3
     // centre row t - R of the window rows t - 2R .. t (ring slot (S + K - i) % K holds row t - i)
-    const int64_t yo = Y0 + t - 2 * R;
-    if (yo < Y0 || yo >= Y1) return;
+    const int32_t orow = t - 2 * R;  // output row relative to Y0
+    if (orow < 0 || orow >= nrows_) return;
     constexpr int c = (S + K - R) % K;
     const uint32_t *C = win_[c];
     uint32_t h;
@@ -177,13 +199,18 @@ struct HmfStrip {
       h = med3(plus, cross, C[2]);
     }
     if (lane < 1 || lane > 30 || x >= W) return;
-    unsigned char *d = out_ + yo * opitch + x * static_cast<int64_t>(sizeof(T));
-    *reinterpret_cast<T *>(d) = static_cast<T>(h & 0xFFFFu);
-    if (x + 1 < W) *reinterpret_cast<T *>(d + sizeof(T)) = static_cast<T>(h >> 16);
+    unsigned char *d = outb_ + static_cast<uint64_t>(static_cast<uint32_t>(orow)) * opitch32_;
+    if (vst_ && x + 1 < W) {  // x is even, so the pair is aligned
+      if constexpr (sizeof(T) == 2) *reinterpret_cast<uint32_t *>(d) = h;
+      else *reinterpret_cast<uint16_t *>(d) = static_cast<uint16_t>((h & 0xFFu) | ((h >> 8) & 0xFF00u));
+    } else {
+      *reinterpret_cast<T *>(d) = static_cast<T>(h & 0xFFFFu);
+      if (x + 1 < W) *reinterpret_cast<T *>(d + sizeof(T)) = static_cast<T>(h >> 16);
+    }
   }
 
   template <int... S>
-  __device__ __forceinline__ void steps(int64_t t0, std::integer_sequence<int, S...>) {
+  __device__ __forceinline__ void steps(int32_t t0, std::integer_sequence<int, S...>) {
     (step<S>(t0 + S), ...);
   }
   template <int... S>
@@ -197,8 +224,8 @@ struct HmfStrip {
     } else {
       loads(std::make_integer_sequence<int, L>{});
     }
-    const int64_t last = Y1 - Y0 + 2 * R;  // steps 0 .. last - 1 cover output rows Y0 .. Y1 - 1
-    for (int64_t t0 = 0; t0 < last; t0 += L) steps(t0, std::make_integer_sequence<int, L>{});
+    const int32_t last = nrows_ + 2 * R;  // steps 0 .. last - 1 cover output rows Y0 .. Y1 - 1
+    for (int32_t t0 = 0; t0 < last; t0 += L) steps(t0, std::make_integer_sequence<int, L>{});
     if constexpr (kAsync) cp_async_wait<0>();  // no copy outlives the warp
   }
 };
