@@ -29,7 +29,7 @@ namespace fx {
 namespace {
 
 constexpr int kHmfOut = 60;    // output columns per strip (lanes 1..30)
-constexpr int kHmfUnitH = 256; // output rows per strip unit
+constexpr int kHmfUnitH = 128; // output rows per strip unit
 constexpr int kHmfWarps = 4;   // warps per CTA
 constexpr int kAsyncRows = 16; // depth of the shared-memory load ring (power of two)
 constexpr unsigned kAll = 0xffffffffu;

@@ -43,10 +43,13 @@ def test_hmf_pitched_and_errors(cuda_lib):
 
 
 @pytest.mark.parametrize("window", [3, 5])
-@pytest.mark.parametrize("shape,bits", [((777, 1001), 12), ((600, 61), 8), ((257, 123), 16)])
+@pytest.mark.parametrize("shape,bits", [((777, 1001), 12), ((600, 61), 8), ((257, 123), 16),
+                                        ((385, 1000), 16), ((300, 522), 8)])
 def test_hmf_multi_unit(cuda_lib, window, shape, bits):
-    """Images spanning several 256-row units and 60-column strips (odd widths,
-    a width one above a strip), against the oracle."""
+    """Images spanning several 128-row units (the last one a single row for 257
+    and 385 rows) and 60-column strips: odd widths (pixel-by-pixel loads, a
+    width one above a strip) and even widths (aligned pair loads: the
+    shared-memory load ring for uint16), against the oracle."""
     h, w = shape
     if bits == 16:
         img = np.random.default_rng(w).integers(0, 65536, size=shape).astype(np.uint16)
@@ -55,3 +58,14 @@ def test_hmf_multi_unit(cuda_lib, window, shape, bits):
                            impulse_frac=0.05, bits=bits)
     got = cuda_lib.hybrid_median(torch.from_numpy(img).cuda(), window).cpu().numpy()
     assert np.array_equal(got, oracle.hybrid_median(img, window))
+
+
+@pytest.mark.parametrize("window", [3, 5])
+def test_hmf_unaligned_output_rows(cuda_lib, window):
+    """An even-width uint16 image whose output rows are 2 bytes off a 4-byte
+    boundary: the lane pairs are written pixel by pixel."""
+    img = np.random.default_rng(window).integers(0, 65536, size=(200, 300)).astype(np.uint16)
+    obuf = torch.full((200, 301), 5, dtype=torch.uint16, device="cuda")  # 602-byte rows
+    cuda_lib.hybrid_median(torch.from_numpy(img).cuda(), window, out=obuf[:, :300])
+    assert np.array_equal(obuf[:, :300].cpu().numpy(), oracle.hybrid_median(img, window))
+    assert (obuf[:, 300].cpu().numpy() == 5).all()
