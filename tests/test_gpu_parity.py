@@ -204,6 +204,38 @@ def test_batch_matches_single_and_oracle(cuda_lib):
         assert_same(singles[i], oracle.extract(np.ascontiguousarray(batch[i][0]), d8), f"oracle image {i}")
 
 
+def test_batch_full_range_16bit_all_groups(cuda_lib):
+    """All four queue groups (uint16 / uint8, aligned pairs / pixel by pixel)
+    in one batch, the uint16 images spanning the full 16-bit range: their
+    strips are recomputed by the batched integer redo kernel (one resident
+    wave striding over the units).  Against single-image calls and the oracle."""
+    rng = np.random.default_rng(41)
+    shapes = [(300, 420, 16), (257, 333, 16), (140, 1000, 8), (211, 97, 8), (90, 64, 16), (77, 53, 8)]
+    imgs = []
+    for h, w, bits in shapes:
+        base = scenes.scene(w, h, seed=h + w, n_rects=max(1, h * w // 400), noise_sigma=4.0 * (1 << (bits - 8)),
+                            impulse_frac=0.01, bits=bits)
+        if bits == 16:  # push part of the image towards the top of the range
+            base[: h // 2] = np.minimum(base[: h // 2].astype(np.int64) + 40000, 65535).astype(np.uint16)
+        imgs.append(base)
+    d, p = pair(4.0)  # features on every image: about 4 % of the uint8 pixels, 30 % of the uint16 ones
+    pairs = [(dev(i), torch.full(i.shape, 9, dtype=torch.uint8, device="cuda")) for i in imgs]
+    singles = [run(cuda_lib, img, p) for img, _ in pairs]
+    with cuda_lib.Plan(p, max_images=8) as plan:
+        for shape in [None, (52, 0, 3), (52, 64, 1)]:
+            if shape:
+                plan.set_tile(*shape)
+            for o in pairs:
+                o[1].fill_(9)
+            plan.extract_batch(pairs)
+            torch.cuda.synchronize()
+            for i, ((_, out), single) in enumerate(zip(pairs, singles)):
+                assert_same(out.cpu().numpy(), single, f"batch image {i} tile {shape}")
+        assert plan.device_status() == 0
+    for i in (0, 1, 2):
+        assert_same(singles[i], oracle.extract(imgs[i], d), f"oracle image {i}")
+
+
 def test_batch_autotune_keeps_results(cuda_lib):
     batch = scenes.uneven_batch(n=6, lo=100, hi=900, seed=8, master_side=1000)
     _, p = pair(16.0)
