@@ -366,3 +366,20 @@ def test_extract_host_batch_matches_device(cuda_lib):
         plan.extract_host_batch(list(zip(hosts, outs2)))
         for o, o2 in zip(outs, outs2):
             assert_same(o2, o, "second call")
+
+
+def test_extract_host_chunk_schedule(cuda_lib):
+    """One 8192^2 uint16 image through the host path: a quarter-size first
+    chunk, full chunks, a shortened chunk and a quarter-size last chunk (from
+    page-locked and from pageable buffers), equal to the device path."""
+    img = scenes.ms_8192_u16_11bit()
+    d, p = pair(8.0)
+    ref = run(cuda_lib, img, p)
+    pinned_in = torch.from_numpy(img).pin_memory()
+    pinned_out = torch.full(img.shape, 9, dtype=torch.uint8).pin_memory()
+    pageable_out = np.full(img.shape, 9, np.uint8)
+    with cuda_lib.Plan(p, max_images=2) as plan:
+        plan.extract_host_batch([(pinned_in.numpy(), pinned_out.numpy())])
+        assert_same(pinned_out.numpy(), ref, "pinned")
+        plan.extract_host_batch([(img, pageable_out)])
+        assert_same(pageable_out, ref, "pageable")
