@@ -182,9 +182,10 @@ typedef struct {
 } fx_image_desc;
 
 /*
- * Many images of uneven sizes and mixed dtypes in ONE persistent launch over
- * a tile queue, replayed from a CUDA graph (the batched form of Sec. 6.2.2's
- * one-thread-per-pixel mapping).  Each image's mask is byte-identical to
+ * Many images of uneven sizes and mixed dtypes in ONE replay of a CUDA graph:
+ * persistent kernels pop work units from a tile queue (one kernel per load
+ * path and pixel type on the streaming path, then the redo pass), the batched
+ * form of Sec. 6.2.2's one-thread-per-pixel mapping.  Each image's mask is byte-identical to
  * fx_extract's.  descs is a HOST array of n descriptors, validated like
  * fx_extract's arguments; the table is copied before the call returns.
  * Output masks must not overlap each other or any input.

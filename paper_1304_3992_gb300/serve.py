@@ -4,7 +4,7 @@ Requests (single-band uint8/uint16 images in host memory) arrive at any time.
 The scheduler admits them in arrival order while their device bytes (image +
 mask) fit the HBM budget, copies each image to the device on a copy stream,
 and launches every request whose copy has finished as one batched
-``fx_extract_batch`` call -- the persistent tile-queue kernel -- on one of
+``fx_extract_batch`` call -- the persistent tile-queue kernels -- on one of
 several compute streams, each with its own plan.  Requests that arrive while
 earlier batches are on the GPU are admitted, copied and launched as soon as
 memory and a compute stream free up, so their work overlaps on the device.
