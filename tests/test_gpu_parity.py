@@ -383,3 +383,19 @@ def test_extract_host_chunk_schedule(cuda_lib):
         assert_same(pinned_out.numpy(), ref, "pinned")
         plan.extract_host_batch([(img, pageable_out)])
         assert_same(pageable_out, ref, "pageable")
+
+
+@pytest.mark.parametrize("hmf", [(), (5,), (3,)])
+def test_tiny_images_hand_cases_gpu(cuda_lib, hmf):
+    """The hand-derived tiny cases of the oracle pins through the library: a
+    one-row step, its one-column transpose and the 2 x 2 steps give the
+    step-edge line at the bright-side pixel; constant tiny images give nothing."""
+    d, p = pair(1.0, t_zc=(0.0, 0.0), t_sd5=(0.0, 0.0), t_sd3=(0.0, 0.0), t_sdmax=(1e9, 1e9), hmf=hmf)
+    for a, b in ((100, 160), (160, 100)):
+        row = np.full((1, 40), a, np.uint16)
+        row[:, 20:] = b
+        sq = np.array([[a, b], [a, b]], np.uint16)
+        for img in (row, row.reshape(40, 1), sq, np.ascontiguousarray(sq.T), np.full((1, 1), a, np.uint16)):
+            got = run(cuda_lib, img, p)
+            assert_same(got, oracle.extract(img, d), f"{img.shape} {a}|{b} hmf={hmf}")
+        assert run(cuda_lib, row, p).nonzero()[1].tolist() == [20 if b > a else 19]

@@ -141,6 +141,32 @@ def test_step_edge_closed_forms(a, b):
     assert out[:, 20 if D > 0 else 19].all()
 
 
+@pytest.mark.parametrize("hmf", [(), (5,), (3,)])
+@pytest.mark.parametrize("a,b", [(100, 160), (160, 100)])
+def test_tiny_images_hand_cases(a, b, hmf):
+    """Hand-derived results for the smallest images (reading R2: every stage
+    replicates its border).  A 1 x N row with a step, its N x 1 transpose and
+    the 2 x 2 steps all extend to an unbounded straight step edge, so each
+    gives the step-edge line of Sec. 3.2 at the bright-side pixel and nothing
+    else (a one-pixel line survives the hybrid median: the '+' group holds the
+    line's replicated column, 5 of 9); a 1 x 1 or constant image gives
+    nothing."""
+    p = params(t_zc=(0.0, 0.0), t_sd5=(0.0, 0.0), t_sd3=(0.0, 0.0), t_sdmax=(1e9, 1e9), hmf=hmf)
+    bright = 1 if b > a else 0
+    row = np.full((1, 40), a, np.uint16)
+    row[:, 20:] = b
+    out = oracle.extract(row, p)
+    assert np.array_equal(out.nonzero()[1], [20 if b > a else 19])
+    assert np.array_equal(oracle.extract(row.reshape(40, 1), p), out.T)
+    sq = np.array([[a, b], [a, b]], np.uint16)
+    expect = np.zeros((2, 2), np.uint8)
+    expect[:, bright] = 1
+    assert np.array_equal(oracle.extract(sq, p), expect)
+    assert np.array_equal(oracle.extract(np.ascontiguousarray(sq.T), p), expect.T)
+    for img in (np.array([[a]], np.uint16), np.full((2, 2), b, np.uint16), np.full((1, 7), a, np.uint16)):
+        assert not oracle.extract(img, p).any()
+
+
 @pytest.mark.parametrize("D", [13, 24, 100, -40])
 def test_step_edge_threshold_boundaries(D):
     """Exactness of the strict thresholds on the step edge: contrast
