@@ -77,14 +77,17 @@ def test_fp32_ragged_sizes(cuda_lib, shape, bits):
     assert tolerance.compare_with_oracle(img, got, d) == 0
 
 
-@pytest.mark.parametrize("case", range(6))
+@pytest.mark.parametrize("case", range(8))
 def test_fp32_parameter_variants(cuda_lib, case):
-    """Median off / 3 / 5 / multi-level and the crossing-map source (these
-    run on the general kernel), other sigmas and mask scales."""
+    """Median off / 3 / 5 then 3 and the crossing-map source (streaming
+    kernel), median 5 then 5 and three levels (general tile kernel), other
+    sigmas and mask scales."""
     img = scenes.scene(180, 140, seed=50 + case, n_rects=40, noise_sigma=16.0, impulse_frac=0.005, bits=12)
     kw = [dict(hmf=()), dict(hmf=(3,)), dict(hmf=(5, 3)),
           dict(stddev_source=1, t_sd5=(0.2, 0.3), t_sdmax=(0.45, 0.5), t_sd3=(0.3, 0.4)),
-          dict(sigma=(1.0, 2.5), t_zc=(9000.0, 20000.0)), dict(mask_q=1000, t_zc=(130000.0, 500000.0))][case]
+          dict(sigma=(1.0, 2.5), t_zc=(9000.0, 20000.0)), dict(mask_q=1000, t_zc=(130000.0, 500000.0)),
+          dict(hmf=(5, 5)), dict(hmf=(5, 3, 3), stddev_source=1, t_sd5=(0.2, 0.3), t_sdmax=(0.45, 0.5),
+                                 t_sd3=(0.3, 0.4))][case]
     d, p = pair(16.0, **kw)
     got = run(cuda_lib, img, p)
     assert tolerance.compare_with_oracle(img, got, d) == 0
