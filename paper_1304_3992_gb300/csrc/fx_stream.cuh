@@ -30,6 +30,9 @@
 // levels (Sec. 3.4, reading R6) run as bitwise logic on those words, and the
 // finished mask rows are stored.  Each 4-row iteration runs a checked body
 // (border fix-ups, clamped loads) only where the strip touches a border.
+// Single-image launches stop computing steps past the last row any output
+// needs (the remaining iterations only shift the bit accumulators); the
+// batched kernels, whose units are long, walk the whole block schedule.
 //
 // Arithmetic is exact with the integer masks: the FP32 path is used while
 // every input value is at most KParams::fbound (all LoG partial sums below
