@@ -71,7 +71,7 @@ class Server:
         self.free_slots = list(range(max_running))
         self.finished = []
         self.batches = []            # sizes of launched batches
-        self.overlapped_launches = 0  # launches made while another batch was on the GPU
+        self.overlapped_launches = 0  # launches made while another batch's event was still pending
 
     # -------------------------------------------------------------- client
     def now(self) -> float:
@@ -157,8 +157,8 @@ class Server:
         while self.ready and self.free_slots:
             batch, self.ready = self.ready[:self.max_batch], self.ready[self.max_batch:]
             slot = self.free_slots.pop(0)
-            if self.running:
-                self.overlapped_launches += 1
+            if any(not self.backend.done(ev) for _, ev, _ in self.running):
+                self.overlapped_launches += 1  # another batch is still executing
             try:
                 ev = self.backend.launch(slot, [r.dev for r in batch])
             except Exception as e:

@@ -42,9 +42,13 @@ def test_served_masks_equal_alone(cuda_lib):
 
 
 def test_batches_overlap_on_the_device(cuda_lib):
+    """A batch of small requests is launched while the big request's batch is
+    still executing (its event pending at launch time: two median levels of
+    radius 2 run on the general kernel, some milliseconds on 8192^2), and
+    every mask equals the lone call's."""
     from paper_1304_3992_gb300.serve import Server, TorchBackend
     fx = cuda_lib
-    p = fx.make_params(fx.FX_U16, 12)
+    p = fx.make_params(fx.FX_U16, 12, hmf=(5, 5))
     big = _pinned(scenes.scene(8192, 8192, seed=43, n_rects=1600, noise_sigma=24, impulse_frac=0.005, bits=12))
     small = [_pinned(big[:300 + 10 * i, :200 + 7 * i]) for i in range(4)]
     be = TorchBackend(p, slots=2, max_images=8)
@@ -55,9 +59,8 @@ def test_batches_overlap_on_the_device(cuda_lib):
     rs = [s.submit(1 + i, im) for i, im in enumerate(small)]
     while any(r.state in ("pending", "copying", "ready") for r in rs):
         s.step()
-    launched_during = r0.state == "running"
     s.drain(release=False)
-    assert s.overlapped_launches >= 1 and launched_during
+    assert s.overlapped_launches >= 1
     for r in [r0] + rs:
         alone = fx.extract(torch.from_numpy(r.image).cuda(), p)
         assert torch.equal(r.dev["out"], alone)
