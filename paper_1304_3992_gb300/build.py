@@ -49,6 +49,7 @@ def _compile(src: str, extra: list[str]) -> str:
     obj = os.path.join(BUILD, os.path.basename(src) + ".o")
     inc = ["-I" + os.path.join(ROOT, "include"), "-I" + CSRC]
     if src.endswith(".cu"):
+        extra = extra + [f"-D{k}={os.environ[k]}" for k in ("FX_FIRST_PASS_CTAS", "FX_WARPS_PER_CTA") if os.environ.get(k)]
         cmd = ["nvcc", ARCH, "-lineinfo", "-O3", "-std=c++17", "-Xcompiler", "-fPIC",
                "-Xcompiler", "-ffp-contract=off", "--expt-relaxed-constexpr", *inc, *extra,
                "-c", src, "-o", obj]

@@ -147,6 +147,24 @@ fx_status make_kparams(const fx_params *p, int32_t maxval, KParams *kp) {
     kp->tt5[f] = tt(kp->tsd5[f]);
     kp->ttmax[f] = tt(kp->tsdmax[f]);
     kp->tt3[f] = tt(kp->tsd3[f]);
+    kp->ntzc1f[f] = -kp->tzc1f[f];
+  }
+  // Sign-bit form of the FP32 path's standard-deviation tests (values <= fbound
+  // <= 4095: D3 <= 20 * 4095^2 < 2^30, D5 <= 156 * 4095^2 < 2^32).  A 3x3
+  // threshold above 2^30 is never reached, so it is clamped there; a 5x5
+  // threshold above 2^31 is reached only by D5 above 2^31, so such
+  // thresholds lower fbound to 3710 (156 * 3710^2 < 2^31) and are clamped too.
+  kp->one = 1u;
+  for (int f = 0; f < 2; ++f) {
+    if (kp->tt3[f] > (1u << 30)) kp->tt3[f] = 1u << 30;
+    if (kp->tt5[f] > (1u << 31) || kp->ttmax[f] > (1u << 31)) {
+      if (kp->fbound > 3710) kp->fbound = 3710;
+      if (kp->tt5[f] > (1u << 31)) kp->tt5[f] = 1u << 31;
+      if (kp->ttmax[f] > (1u << 31)) kp->ttmax[f] = 1u << 31;
+    }
+    kp->ntt3[f] = 0u - kp->tt3[f];
+    kp->ntt5[f] = 0u - kp->tt5[f];
+    kp->nttmax[f] = 0u - kp->ttmax[f];
   }
   kp->sd_same = kp->tsd5[0] == kp->tsd5[1] && kp->tsdmax[0] == kp->tsdmax[1] && kp->tsd3[0] == kp->tsd3[1];
   // crossing-map source: the counts n in [0, Lambda] with n (Lambda - n) > t form

@@ -36,6 +36,13 @@ struct KParams {
   float tzc1f[2];
   // 32-bit standard-deviation tests for the FP32 path: s > T  <=>  D >= tt.
   uint32_t tt5[2], ttmax[2], tt3[2];
+  // The same tests as sign bits: with r = D - tt (mod 2^32), D3 < 2^31 and
+  // tt3 <= 2^30, D3 < tt3 <=> r3 < 0; D5 < 2^32 and tt5, ttmax <= 2^31, so
+  // D5 < tt <=> (D5 < 2^31 and r < 0).  ntt* = -tt* (mod 2^32); one = 1 (an
+  // opaque multiplier, so the subtraction stays a multiply-add).
+  uint32_t ntt5[2], nttmax[2], ntt3[2], one;
+  // -tzc1f, the contrast threshold of the FP32 path added to max - min
+  float ntzc1f[2];
   int32_t sd_same;   // both branches use the same standard-deviation thresholds
   // FP32-LoG mode (fx_params.log_mode): ringf holds the non-integer mask's ring
   // weights and L is evaluated in FP32 from d_c = R_c - n_c I(p); the contrast

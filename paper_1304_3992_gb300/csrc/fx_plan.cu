@@ -98,7 +98,7 @@ __global__ void __launch_bounds__(256) batch_kernel_general(const unsigned char 
 // strip loop (the register allocation and instruction working set of the
 // single-image kernel).
 template <typename T, bool kF32Log, bool kPair, bool kSd2, bool kSrcZ>
-__global__ void __launch_bounds__(32 * kWarpsPerCta, 3) batch_kernel_fast(const unsigned char *table,
+__global__ void __launch_bounds__(32 * kWarpsPerCta, kFirstPassCtas) batch_kernel_fast(const unsigned char *table,
                                                                       unsigned long long *counter, int *status,
                                                                       const __grid_constant__ KParams kp) {
   __shared__ StripWords words;
@@ -427,7 +427,7 @@ fx_status fx_plan_create(fx_plan **out, const fx_params *params, int32_t max_ima
   p->max_images = max_images;
   p->unit_w = strip_width(p->kp8.source == 1);
   p->unit_h = kDefaultUnitH;
-  p->ctas_per_sm = p->fast ? 3 : 2;
+  p->ctas_per_sm = p->fast ? kFirstPassCtas : 2;
   p->auto_h = true;
   if (cudaSetDevice(device) != cudaSuccess || cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
     delete p;

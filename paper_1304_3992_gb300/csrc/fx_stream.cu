@@ -9,7 +9,7 @@ namespace {
 // The first pass runs 3 CTAs (12 warps) per SM in 168 registers; the redo
 // pass (64-bit sums) runs 2 per SM, where it needs no spill.
 template <typename T, bool kRedoPass, bool kF32Log, bool kPair, bool kSd2, bool kSrcZ>
-__global__ void __launch_bounds__(32 * kWarpsPerCta, kRedoPass ? 2 : 3) stream_kernel(const __grid_constant__ ImageView v,
+__global__ void __launch_bounds__(32 * kWarpsPerCta, kRedoPass ? 2 : kFirstPassCtas) stream_kernel(const __grid_constant__ ImageView v,
                                                                   const __grid_constant__ KParams kp,
                                                                   int64_t units_x, int64_t units, int uh) {
   __shared__ StripWords words;
@@ -77,7 +77,7 @@ int64_t warp_slots() {
   if (!slots[dev]) {
     int sms = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 152;
-    slots[dev] = static_cast<int64_t>(sms) * 3 * kWarpsPerCta;
+    slots[dev] = static_cast<int64_t>(sms) * kFirstPassCtas * kWarpsPerCta;
   }
   return slots[dev];
 }

@@ -56,7 +56,16 @@ constexpr int kDefaultUnitH = 512;
 constexpr int kNumUnitHeights = 4;
 constexpr int kUnitHeights[kNumUnitHeights] = {256, 512, 768, 1024};
 constexpr int kMaxCtasPerSm = 8;
-constexpr int kWarpsPerCta = 4;
+#ifndef FX_WARPS_PER_CTA
+#define FX_WARPS_PER_CTA 4
+#endif
+constexpr int kWarpsPerCta = FX_WARPS_PER_CTA;
+// CTAs per SM of the streaming first pass (its __launch_bounds__ and the wave
+// model of the unit height)
+#ifndef FX_FIRST_PASS_CTAS
+#define FX_FIRST_PASS_CTAS 3
+#endif
+constexpr int kFirstPassCtas = FX_FIRST_PASS_CTAS;
 
 inline bool fast_unit_shape_ok(int w, int h, bool src_z) {
   return w == strip_width(src_z) && h >= 16 && h <= 8192 && h % 16 == 0;
@@ -118,7 +127,10 @@ __device__ __forceinline__ void put(uint32_t &acc, uint32_t v) { acc = __funnels
 // Arithmetic of a strip.  kModeF32 / kModeInt: integer masks, exact FP32 or
 // int32 / int64 arithmetic.  kModeF32Log / kModeF32LogWide: the FP32-LoG mode
 // (non-integer masks, L rounded in FP32), with 32-bit or 64-bit sums for the
-// exact standard-deviation test.
+// exact standard-deviation test.  Values of the lane's two columns travel as
+// a pair P: on the FP32 paths a float2, so that every linear operation is one
+// packed FP32x2 instruction (IEEE round-to-nearest per element, hence the same
+// results as two scalar operations); on the integer path two int32.
 enum : int { kModeF32 = 0, kModeInt = 1, kModeF32Log = 2, kModeF32LogWide = 3 };
 
 template <int kMode>
@@ -130,15 +142,25 @@ struct Ar<kModeF32> {
   static constexpr bool kRel = false;     // L from the ring sums R_c directly
   static constexpr bool kChecked = true;  // values above fbound send the strip to the redo pass
   // Eq. 2 sums of squares are taken over the biased bits K + u (K = 0x4B000000,
-  // the bits of the FP32 value u + 2^23) and the bias is removed in sdpass.
+  // the bits of the FP32 value u + 2^23) and the bias is removed in sdfail.
   static constexpr bool kBiased = true;
   using V = float;
+  using P = float2;
   using Q = uint32_t;
+  static __device__ __forceinline__ P mk(V a, V b) { return make_float2(a, b); }
+  static __device__ __forceinline__ V lo(P p) { return p.x; }
+  static __device__ __forceinline__ V hi(P p) { return p.y; }
+  static __device__ __forceinline__ P add(P a, P b) { return __fadd2_rn(a, b); }
+  static __device__ __forceinline__ V add1(V a, V b) { return __fadd_rn(a, b); }
+  // w x + y (one rounding per element)
+  static __device__ __forceinline__ P fma(V w, P x, P y) { return __ffma2_rn(make_float2(w, w), x, y); }
+  static __device__ __forceinline__ P zero() { return make_float2(0.0f, 0.0f); }
   static __device__ __forceinline__ V cvt(uint32_t u) { return __uint_as_float(0x4B000000u | u) - 8388608.0f; }
   static __device__ __forceinline__ Q sq(uint32_t u) { return u * u; }
   static __device__ __forceinline__ V w(const KParams &kp, int f, int c) { return kp.ringf[f][c]; }
   static __device__ __forceinline__ uint32_t bits(V x) { return __float_as_uint(x); }
-  static __device__ __forceinline__ V neg(V x) { return 0.0f - x; }
+  // 0 - x (+0 for x = 0: no response is ever -0)
+  static __device__ __forceinline__ P neg(P x) { return __ffma2_rn(x, make_float2(-1.0f, -1.0f), zero()); }
   static __device__ __forceinline__ V max3(V a, V b, V c) {
     float d;
     asm("max.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
@@ -149,24 +171,41 @@ struct Ar<kModeF32> {
     asm("min.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
     return d;
   }
-  // sign bit set  <=>  max - min <= t_zc  (contrast test fails)
-  static __device__ __forceinline__ uint32_t cfail(const KParams &kp, int f, V mx, V mn) {
-    return __float_as_uint((mx - mn) - kp.tzc1f[f]);
+  // sign bits set  <=>  max - min <= t_zc  (contrast test fails), both columns
+  static __device__ __forceinline__ P cfail(const KParams &kp, int f, P mx, P mn) {
+    const P d = __ffma2_rn(mn, make_float2(-1.0f, -1.0f), mx);  // max - min, rounded once
+    return __fadd2_rn(d, make_float2(kp.ntzc1f[f], kp.ntzc1f[f]));
   }
-  // sign bit set  <=>  the standard-deviation test passes (reading R4).
+  // Sign bits set  <=>  the standard-deviation test fails (reading R4), for
+  // both columns (A3, A5: pixel sums; Q3, Q5: sums of the squared biased bits).
   // Q = sum (K + u)^2 = sum u^2 + 2K A (mod 2^32, as K^2 = 0), so
   // D = Lambda sum u^2 - A^2 = Lambda Q - b (b + c)  with b = K + A = bits(A + 2^23)
   // and c = 16K (Lambda = 9) or 48K (Lambda = 25); -b - c is the bit pattern of
   // one exact FFMA of A (2^-117 - A 2^-141, resp. A 2^-77 - 2^-53).  D < 2^32.
-  static __device__ __forceinline__ uint32_t sdpass(const KParams &kp, int f, V A3, V A5, Q Q3, Q Q5) {
-    const uint32_t b3 = __float_as_uint(A3 + 8388608.0f), b5 = __float_as_uint(A5 + 8388608.0f);
-    const uint32_t n3 = __float_as_uint(__fmaf_rn(A3, -0x1p-141f, 0x1p-117f));
-    const uint32_t n5 = __float_as_uint(__fmaf_rn(A5, 0x1p-77f, -0x1p-53f));
-    const uint32_t d3 = Q3 * 9u + b3 * n3;
-    const uint32_t d5 = Q5 * 25u + b5 * n5;
-    const bool pass = d5 >= kp.ttmax[f] ? d3 >= kp.tt3[f] : d5 >= kp.tt5[f];
-    return pass ? 0x80000000u : 0u;
+  // The three threshold tests come out as sign bits (KParams::ntt*) and the
+  // gate S = (s5 > t_sdmax) ? (s3 > t_sd3) : (s5 > t_sd5) is a bitwise select.
+  static __device__ __forceinline__ void sdfail(const KParams &kp, int f, P A3, P A5, const Q Q3[2],
+                                                const Q Q5[2], uint32_t out[2]) {
+    const P B3 = __fadd2_rn(A3, make_float2(8388608.0f, 8388608.0f));
+    const P B5 = __fadd2_rn(A5, make_float2(8388608.0f, 8388608.0f));
+    const P N3 = __ffma2_rn(A3, make_float2(-0x1p-141f, -0x1p-141f), make_float2(0x1p-117f, 0x1p-117f));
+    const P N5 = __ffma2_rn(A5, make_float2(0x1p-77f, 0x1p-77f), make_float2(-0x1p-53f, -0x1p-53f));
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const uint32_t b3 = __float_as_uint(j ? B3.y : B3.x), n3 = __float_as_uint(j ? N3.y : N3.x);
+      const uint32_t b5 = __float_as_uint(j ? B5.y : B5.x), n5 = __float_as_uint(j ? N5.y : N5.x);
+      const uint32_t r3 = Q3[j] * 9u + (b3 * n3 + kp.ntt3[f]);  // D3 - tt3
+      const uint32_t d5 = Q5[j] * 25u + b5 * n5;
+      const uint32_t r5 = d5 + kp.ntt5[f], rm = d5 + kp.nttmax[f];  // D5 - tt5, D5 - ttmax
+      const uint32_t g = ~d5 & rm;          // bit 31: D5 < ttmax
+      out[j] = (g & r5) | (~g & r3);       // bit 31: the selected test fails
+    }
   }
+};
+
+// Pair of int32 for the integer path.
+struct I2 {
+  int32_t x, y;
 };
 
 // Integer path: any uint16 value (|L| < 2^30 by the plan's range check).
@@ -176,22 +215,37 @@ struct Ar<kModeInt> {
   static constexpr bool kChecked = false;
   static constexpr bool kBiased = false;
   using V = int32_t;
+  using P = I2;
   using Q = uint64_t;
+  static __device__ __forceinline__ P mk(V a, V b) { return P{a, b}; }
+  static __device__ __forceinline__ V lo(P p) { return p.x; }
+  static __device__ __forceinline__ V hi(P p) { return p.y; }
+  static __device__ __forceinline__ P add(P a, P b) { return P{a.x + b.x, a.y + b.y}; }
+  static __device__ __forceinline__ V add1(V a, V b) { return a + b; }
+  static __device__ __forceinline__ P fma(V w, P x, P y) { return P{w * x.x + y.x, w * x.y + y.y}; }
+  static __device__ __forceinline__ P zero() { return P{0, 0}; }
   static __device__ __forceinline__ V cvt(uint32_t u) { return static_cast<int32_t>(u); }
   static __device__ __forceinline__ Q sq(uint32_t u) { return static_cast<uint64_t>(u) * u; }
   static __device__ __forceinline__ V w(const KParams &kp, int f, int c) { return kp.ring[f][c]; }
   static __device__ __forceinline__ uint32_t bits(V x) { return static_cast<uint32_t>(x); }
-  static __device__ __forceinline__ V neg(V x) { return -x; }
+  static __device__ __forceinline__ P neg(P x) { return P{-x.x, -x.y}; }
   static __device__ __forceinline__ V max3(V a, V b, V c) { return max(max(a, b), c); }
   static __device__ __forceinline__ V min3(V a, V b, V c) { return min(min(a, b), c); }
-  static __device__ __forceinline__ uint32_t cfail(const KParams &kp, int f, V mx, V mn) {
-    return static_cast<uint32_t>(mx - mn) - static_cast<uint32_t>(kp.tzc[f]) - 1u;
+  static __device__ __forceinline__ P cfail(const KParams &kp, int f, P mx, P mn) {
+    const uint32_t t = static_cast<uint32_t>(kp.tzc[f]) + 1u;
+    return P{static_cast<int32_t>(static_cast<uint32_t>(mx.x - mn.x) - t),
+             static_cast<int32_t>(static_cast<uint32_t>(mx.y - mn.y) - t)};
   }
-  static __device__ __forceinline__ uint32_t sdpass(const KParams &kp, int f, V A3, V A5, Q Q3, Q Q5) {
-    const int64_t d3 = 9 * static_cast<int64_t>(Q3) - static_cast<int64_t>(A3) * A3;
-    const int64_t d5 = 25 * static_cast<int64_t>(Q5) - static_cast<int64_t>(A5) * A5;
-    const bool pass = d5 > kp.tsdmax[f] ? d3 > kp.tsd3[f] : d5 > kp.tsd5[f];
-    return pass ? 0x80000000u : 0u;
+  static __device__ __forceinline__ void sdfail(const KParams &kp, int f, P A3, P A5, const Q Q3[2],
+                                                const Q Q5[2], uint32_t out[2]) {
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const int64_t a3 = j ? A3.y : A3.x, a5 = j ? A5.y : A5.x;
+      const int64_t d3 = 9 * static_cast<int64_t>(Q3[j]) - a3 * a3;
+      const int64_t d5 = 25 * static_cast<int64_t>(Q5[j]) - a5 * a5;
+      const bool pass = d5 > kp.tsdmax[f] ? d3 > kp.tsd3[f] : d5 > kp.tsd5[f];
+      out[j] = pass ? 0u : 0x80000000u;
+    }
   }
 };
 
@@ -211,14 +265,18 @@ struct Ar<kModeF32LogWide> : Ar<kModeF32> {
   static constexpr bool kBiased = false;
   using Q = uint64_t;
   static __device__ __forceinline__ Q sq(uint32_t u) { return static_cast<uint64_t>(u) * u; }
-  static __device__ __forceinline__ uint32_t sdpass(const KParams &kp, int f, V A3, V A5, Q Q3, Q Q5) {
-    // A3, A5 are exact integers below 2^21
-    const int64_t a3 = static_cast<int64_t>(__float_as_uint(A3 + 8388608.0f) - 0x4B000000u);
-    const int64_t a5 = static_cast<int64_t>(__float_as_uint(A5 + 8388608.0f) - 0x4B000000u);
-    const int64_t d3 = 9 * static_cast<int64_t>(Q3) - a3 * a3;
-    const int64_t d5 = 25 * static_cast<int64_t>(Q5) - a5 * a5;
-    const bool pass = d5 > kp.tsdmax[f] ? d3 > kp.tsd3[f] : d5 > kp.tsd5[f];
-    return pass ? 0x80000000u : 0u;
+  static __device__ __forceinline__ void sdfail(const KParams &kp, int f, P A3, P A5, const Q Q3[2],
+                                                const Q Q5[2], uint32_t out[2]) {
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      // A3, A5 are exact integers below 2^21
+      const int64_t a3 = static_cast<int64_t>(__float_as_uint((j ? A3.y : A3.x) + 8388608.0f) - 0x4B000000u);
+      const int64_t a5 = static_cast<int64_t>(__float_as_uint((j ? A5.y : A5.x) + 8388608.0f) - 0x4B000000u);
+      const int64_t d3 = 9 * static_cast<int64_t>(Q3[j]) - a3 * a3;
+      const int64_t d5 = 25 * static_cast<int64_t>(Q5[j]) - a5 * a5;
+      const bool pass = d5 > kp.tsdmax[f] ? d3 > kp.tsd3[f] : d5 > kp.tsd5[f];
+      out[j] = pass ? 0u : 0x80000000u;
+    }
   }
 };
 
@@ -237,6 +295,7 @@ struct Strip {
   // output columns: 2 LoG + 1 crossing (+ 2 standard deviation) + up to 3 median
   static constexpr int kLeftHalo = kSrcZ ? 8 : 6, kOutCols = strip_width(kSrcZ);
   using V = typename A::V;
+  using P = typename A::P;
   using Q = typename A::Q;
 
   const ImageView &v;
@@ -247,13 +306,14 @@ struct Strip {
   int bl_lane, bl_slot, br_lane, br_slot;
   uint32_t outmask_l, outmask_r;  // this lane's slots left of / right of the image (M0 << j)
 
-  // Rings of period 4 (slot of row t = t & 3).  The row four steps back is
-  // read before the newest row overwrites its slot.
-  V f_[4][2], h1_[4][2], h2_[4][2];
+  // Rings of period 4 (slot of row t = t & 3), one pair (the lane's two
+  // columns) per row.  The row four steps back is read before the newest row
+  // overwrites its slot; sums over it are taken first, so that the new row can
+  // take its registers.
+  P f_[4], h1_[4], h2_[4];
   Q c3_[4][2], c5_[4][2];
-  V L_[2][4][2];
-  V LW_[2][4], LE_[2][4];
-  uint32_t S_[2][4][2];
+  P L_[2][4];
+  uint32_t S_[2][4][2];  // sign bit: the standard-deviation test fails
   uint32_t raw_[4], raw1_[4];  // loaded pixels of rows t..t+3 (raw1_: second pixel, !kPair)
   uint32_t vmax_;
   uint32_t acc_[12];
@@ -266,6 +326,11 @@ struct Strip {
   uint32_t (*sw_)[32];
   static constexpr int kBlk = 0, kPneg = 12, kPpos = 14, kPsS = 16, kMA = 18, kMB = 19, kHA = 20, kHB = 21,
                        kZA = 22, kZB = 24, kPcf = 26, kWords = 28;
+  // kAsync (uint16 pixel pairs on the FP32 paths): the input rows arrive in an
+  // 8-row ring of words in shared memory (kRing .. kRing + 7), filled by
+  // cp.async seven rows ahead, so loads in flight hold no registers.
+  static constexpr bool kAsync = sizeof(T) == 2 && kPair && A::kBiased;
+  static constexpr int kRing = kWords, kRingRows = 8;
   __device__ __forceinline__ uint32_t &blk(int i) { return sw_[kBlk + i][lane]; }
 
   // load state: rows relative to Y0; p0_ / p1_ address row rbase
@@ -273,6 +338,12 @@ struct Strip {
   const unsigned char *p0_, *p1_;
   uint32_t pitch32;
   uint32_t sel_;  // kPair: byte selector taking the clamped columns out of the loaded pair
+  // byte selectors making the biased bits K + u of the lane's two pixels from
+  // the loaded word(s) and K (A::kBiased)
+  uint32_t selb0_, selb1_;
+  // kAsync: shared-memory address of this lane's word in ring slot 4 (k & 1)
+  // (slots 4 (k & 1) + S hold the rows of iteration k) and in the other half
+  uint32_t ring_h_, ring_o_;
 
   __device__ Strip(const ImageView &v_, const KParams &kp_, int64_t x0, int64_t y0, int64_t y1,
                    uint32_t (*words)[32])
@@ -310,26 +381,34 @@ struct Strip {
       const int64_t cb = (d0 < W - 2 ? d0 : W - 2) & ~int64_t{1};
       p0_ = p1_ = base + cb * static_cast<int64_t>(sizeof(T));
       const uint32_t h0 = static_cast<uint32_t>(d0 - cb), h1 = static_cast<uint32_t>(d1 - cb);
-      if constexpr (sizeof(T) == 2) sel_ = (h0 ? 0x32u : 0x10u) | ((h1 ? 0x32u : 0x10u) << 8);
-      else sel_ = h0 | 0x40u | (h1 << 8) | 0x4000u;
+      if constexpr (sizeof(T) == 2) {
+        sel_ = (h0 ? 0x32u : 0x10u) | ((h1 ? 0x32u : 0x10u) << 8);
+        selb0_ = h0 ? 0x7432u : 0x7410u;
+        selb1_ = h1 ? 0x7432u : 0x7410u;
+      } else {
+        sel_ = h0 | 0x40u | (h1 << 8) | 0x4000u;
+        selb0_ = 0x7440u | h0;
+        selb1_ = 0x7440u | h1;
+      }
     } else {
       p0_ = base + d0 * static_cast<int64_t>(sizeof(T));
       p1_ = base + d1 * static_cast<int64_t>(sizeof(T));
       sel_ = 0x5410u;
+      selb0_ = selb1_ = 0x7410u;  // each load holds one zero-extended pixel
     }
     vmax_ = 0;
     for (int i = 0; i < 12; ++i) acc_[i] = 0;
     for (int i = 0; i < kWords; ++i) sw_[i][lane] = 0;
+    ring_h_ = ring_o_ = static_cast<uint32_t>(__cvta_generic_to_shared(&sw_[kRing][lane]));
 #pragma unroll
     for (int s = 0; s < 4; ++s) {
+      f_[s] = h1_[s] = h2_[s] = A::zero();
+      L_[0][s] = L_[1][s] = A::zero();
 #pragma unroll
       for (int j = 0; j < 2; ++j) {
-        f_[s][j] = h1_[s][j] = h2_[s][j] = V(0);
         c3_[s][j] = c5_[s][j] = Q(0);
-        L_[0][s][j] = L_[1][s][j] = V(0);
         S_[0][s][j] = S_[1][s][j] = 0;
       }
-      LW_[0][s] = LW_[1][s] = LE_[0][s] = LE_[1][s] = V(0);
       raw_[s] = raw1_[s] = 0;
     }
   }
@@ -348,6 +427,19 @@ struct Strip {
       raw_[S] = __ldg(reinterpret_cast<const T *>(p0_ + off));
       raw1_[S] = __ldg(reinterpret_cast<const T *>(p1_ + off));
     }
+  }
+
+  // kAsync: row t (relative to Y0) into the ring word at shared address dst
+  // (clamped like load_row), as one cp.async commit group.
+  template <bool kClamp = true>
+  __device__ __forceinline__ void load_row_async(uint32_t dst, int32_t tr) {
+    const int32_t yr = kClamp ? (tr < rlo ? rlo : (tr > rhi ? rhi : tr)) : tr;
+    const uint64_t off = static_cast<uint64_t>(static_cast<uint32_t>(yr - rbase)) * pitch32;
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n\tcp.async.commit_group;" ::"r"(dst), "l"(p0_ + off)
+                 : "memory");
+  }
+  __device__ __forceinline__ void async_drain() {
+    if constexpr (kAsync) asm volatile("cp.async.wait_group 0;" ::: "memory");
   }
 
   // The lane's two pixels of the row in slot S as a 16-bit pair (column 0 low).
@@ -373,6 +465,12 @@ struct Strip {
     }
   }
 
+  __device__ __forceinline__ void fix_cols(P &x) {
+    V a[2] = {A::lo(x), A::hi(x)};
+    fix_cols(a);
+    x = A::mk(a[0], a[1]);
+  }
+
   // Same for a mask word: columns outside the image take the border column's bits.
   __device__ __forceinline__ uint32_t fix_cols_bits(uint32_t m) {
     const uint32_t ml = __shfl_sync(kFull, m, bl_lane);
@@ -388,36 +486,57 @@ struct Strip {
   // or rows next to the first or last image row); otherwise they are no-ops.
   template <int S, bool kChk>
   __device__ __forceinline__ void step(int32_t t) {  // t relative to Y0, S = t & 3
-    const uint32_t w = pixels<S>();
-    load_row<S, kChk>(t + 4);  // four rows ahead, into the slot just read
-    if (check) vmax_ = __vmaxu2(vmax_, w);
-    const uint32_t hl = __shfl_up_sync(kFull, w, 1);    // columns -2, -1
-    const uint32_t hr = __shfl_down_sync(kFull, w, 1);  // columns 2, 3
-    V fv[6];
+    constexpr int c0 = (S + 2) & 3, m1 = (S + 1) & 3, p1 = (S + 3) & 3;  // rows t-2, t-3, t-1
+    // Row t: F = the lane's two pixels (columns 0, 1), Fl / Fr = columns -2, -1
+    // / 2, 3 (the neighbouring lanes' pixels), c3n / c5n = the 3- and 5-wide
+    // sums of squares per column.
+    P F, Fl, Fr;
     Q c3n[2] = {}, c5n[2] = {};
     if constexpr (A::kBiased) {
-      // biased bits K + u of the six pixels (columns -2 .. 3); FP32 value = bits - 2^23
-      const uint32_t b[6] = {__byte_perm(hl, 0x4B000000u, 0x7610), __byte_perm(hl, 0x4B000000u, 0x7632),
-                             __byte_perm(w, 0x4B000000u, 0x7610), __byte_perm(w, 0x4B000000u, 0x7632),
-                             __byte_perm(hr, 0x4B000000u, 0x7610), __byte_perm(hr, 0x4B000000u, 0x7632)};
-#pragma unroll
-      for (int k = 0; k < 6; ++k) fv[k] = __uint_as_float(b[k]) - 8388608.0f;
+      // biased bits K + u (K = 0x4B000000; FP32 value u + 2^23) straight from the
+      // loaded word(s), before the load ahead refills the slot
+      uint32_t r0, r1;
+      if constexpr (kAsync) {
+        // row t is in ring slot t & 7 = 4 (k & 1) + S; six younger rows may be in flight
+        asm volatile("cp.async.wait_group 6;\n\tld.shared.u32 %0, [%1];" : "=r"(r0) : "r"(ring_h_ + 128u * S) : "memory");
+        r1 = r0;
+        // refill the slot of row t - 1 (read one step ago) with row t + 7
+        load_row_async<kChk>(S == 0 ? ring_o_ + 384u : ring_h_ + 128u * (S - 1), t + kRingRows - 1);
+      } else {
+        r0 = raw_[S];
+        r1 = raw1_[S];
+      }
+      const uint32_t b2 = __byte_perm(r0, 0x4B000000u, selb0_);
+      const uint32_t b3 = __byte_perm(kPair ? r0 : r1, 0x4B000000u, selb1_);
+      if (check) vmax_ = __vmaxu2(vmax_, kPair ? r0 : __byte_perm(r0, r1, 0x5410));
+      if constexpr (!kAsync) load_row<S, kChk>(t + 4);
+      const uint32_t b0 = __shfl_up_sync(kFull, b2, 1), b1 = __shfl_up_sync(kFull, b3, 1);
+      const uint32_t b4 = __shfl_down_sync(kFull, b2, 1), b5 = __shfl_down_sync(kFull, b3, 1);
+      const P bias = A::mk(-8388608.0f, -8388608.0f);
+      F = A::add(A::mk(__uint_as_float(b2), __uint_as_float(b3)), bias);
+      Fl = A::add(A::mk(__uint_as_float(b0), __uint_as_float(b1)), bias);
+      Fr = A::add(A::mk(__uint_as_float(b4), __uint_as_float(b5)), bias);
       if constexpr (!kSrcZ) {
-        const uint32_t s23 = b[2] * b[2] + b[3] * b[3];
-        c3n[0] = b[1] * b[1] + s23;
-        c3n[1] = b[4] * b[4] + s23;
-        c5n[0] = b[0] * b[0] + (b[4] * b[4] + c3n[0]);
-        c5n[1] = b[5] * b[5] + (b[1] * b[1] + c3n[1]);
+        const uint32_t s23 = b2 * b2 + b3 * b3;
+        c3n[0] = b1 * b1 + s23;
+        c3n[1] = b4 * b4 + s23;
+        c5n[0] = b0 * b0 + (b4 * b4 + c3n[0]);
+        c5n[1] = b5 * b5 + (b1 * b1 + c3n[1]);
       }
     } else {
+      const uint32_t w = pixels<S>();
+      load_row<S, kChk>(t + 4);  // four rows ahead, into the slot just read
+      if (check) vmax_ = __vmaxu2(vmax_, w);
+      const uint32_t hl = __shfl_up_sync(kFull, w, 1);    // columns -2, -1
+      const uint32_t hr = __shfl_down_sync(kFull, w, 1);  // columns 2, 3
       const uint32_t u[6] = {hl & 0xFFFFu, hl >> 16, w & 0xFFFFu, w >> 16, hr & 0xFFFFu, hr >> 16};
-      Q sq[6];
-#pragma unroll
-      for (int k = 0; k < 6; ++k) {
-        fv[k] = A::cvt(u[k]);
-        sq[k] = A::sq(u[k]);
-      }
+      Fl = A::mk(A::cvt(u[0]), A::cvt(u[1]));
+      F = A::mk(A::cvt(u[2]), A::cvt(u[3]));
+      Fr = A::mk(A::cvt(u[4]), A::cvt(u[5]));
       if constexpr (!kSrcZ) {
+        Q sq[6];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) sq[k] = A::sq(u[k]);
 #pragma unroll
         for (int j = 0; j < 2; ++j) {
           c3n[j] = sq[j + 1] + sq[j + 2] + sq[j + 3];
@@ -425,82 +544,78 @@ struct Strip {
         }
       }
     }
-    V fn[2], h1n[2], h2n[2];
+    // Sums over row t - 4 (slot S), taken before row t takes its slot.
+    const P T4 = A::add(h2_[c0], f_[S]);                     // R4 without row t
+    const P T5 = A::add(A::add(h2_[m1], h2_[p1]), h1_[S]);   // R5 without row t
+    const P T8 = A::add(h2_[S], Fl);                         // R8 without column +2 of row t
+    Q P5[2];
+#pragma unroll
+    for (int j = 0; j < 2; ++j) P5[j] = c5_[S][j] + c5_[m1][j] + c5_[c0][j];
+    // horizontal sums of row t: h1 = I(x-1) + I(x+1), h2 = I(x-2) + I(x+2)
+    f_[S] = F;
+    h1_[S] = A::mk(A::add1(A::hi(Fl), A::hi(F)), A::add1(A::lo(F), A::lo(Fr)));
+    h2_[S] = A::add(Fl, Fr);
 #pragma unroll
     for (int j = 0; j < 2; ++j) {
-      fn[j] = fv[j + 2];
-      h1n[j] = fv[j + 1] + fv[j + 3];
-      h2n[j] = fv[j] + fv[j + 4];
-    }
-    centre<S, kChk>(t - 2, fn, h1n, h2n, c5n);
-#pragma unroll
-    for (int j = 0; j < 2; ++j) {
-      f_[S][j] = fn[j];
-      h1_[S][j] = h1n[j];
-      h2_[S][j] = h2n[j];
       c3_[S][j] = c3n[j];
       c5_[S][j] = c5n[j];
     }
+    centre<S, kChk>(t - 2, T4, T5, A::add(T8, Fr), P5);
     pack<S>();
   }
 
   // LoG responses and the standard-deviation test for the centre row c = t - 2
-  // (row t arrives in fn / h1n / h2n / c5n; slot S still holds row t - 4).
+  // (row t is in slot S; T4 / T5 / R8: the sums that involve row t - 4).
   template <int S, bool kChk>
-  __device__ __forceinline__ void centre(int32_t c, const V fn[2], const V h1n[2], const V h2n[2],
-                                         const Q c5n[2]) {
-    constexpr int c0 = (S + 2) & 3, m1 = (S + 1) & 3, p1 = (S + 3) & 3, m2 = S;
+  __device__ __forceinline__ void centre(int32_t c, P T4, P T5, P R8, const Q P5[2]) {
+    constexpr int c0 = (S + 2) & 3, m1 = (S + 1) & 3, p1 = (S + 3) & 3;
+    // the six ring sums (squared radii 0, 1, 2, 4, 5, 8) of the radial masks
+    const P R0 = f_[c0];
+    const P R1 = A::add(h1_[c0], A::add(f_[m1], f_[p1]));
+    const P R2 = A::add(h1_[m1], h1_[p1]);
+    const P R4 = A::add(T4, f_[S]);
+    const P R5 = A::add(T5, h1_[S]);
 #pragma unroll
-    for (int j = 0; j < 2; ++j) {
-      const V R0 = f_[c0][j];
-      const V R1 = h1_[c0][j] + (f_[m1][j] + f_[p1][j]);
-      const V R2 = h1_[m1][j] + h1_[p1][j];
-      const V R4 = h2_[c0][j] + (f_[m2][j] + fn[j]);
-      const V R5 = (h2_[m1][j] + h2_[p1][j]) + (h1_[m2][j] + h1n[j]);
-      const V R8 = h2_[m2][j] + h2n[j];
+    for (int f = 0; f < 2; ++f) {
       if constexpr (A::kRel) {
         // FP32-LoG: one rounding per product-add, in the order of the ring radii
-        const float d1 = __fmaf_rn(-4.0f, R0, R1), d2 = __fmaf_rn(-4.0f, R0, R2);
-        const float d4 = __fmaf_rn(-4.0f, R0, R4), d5 = __fmaf_rn(-8.0f, R0, R5);
-        const float d8 = __fmaf_rn(-4.0f, R0, R8);
-#pragma unroll
-        for (int f = 0; f < 2; ++f) {
-          // starting from +0: a zero product gives +0, so no sum is ever -0
-          float l = __fmaf_rn(A::w(kp, f, 1), d1, 0.0f);
-          l = __fmaf_rn(A::w(kp, f, 2), d2, l);
-          l = __fmaf_rn(A::w(kp, f, 3), d4, l);
-          l = __fmaf_rn(A::w(kp, f, 4), d5, l);
-          L_[f][c0][j] = __fmaf_rn(A::w(kp, f, 5), d8, l);
-        }
+        const P d1 = A::fma(-4.0f, R0, R1), d2 = A::fma(-4.0f, R0, R2);
+        const P d4 = A::fma(-4.0f, R0, R4), d5 = A::fma(-8.0f, R0, R5);
+        const P d8 = A::fma(-4.0f, R0, R8);
+        // starting from +0: a zero product gives +0, so no sum is ever -0
+        P l = A::fma(A::w(kp, f, 1), d1, A::zero());
+        l = A::fma(A::w(kp, f, 2), d2, l);
+        l = A::fma(A::w(kp, f, 3), d4, l);
+        l = A::fma(A::w(kp, f, 4), d5, l);
+        L_[f][c0] = A::fma(A::w(kp, f, 5), d8, l);
       } else {
+        // exact partial sums; starting from +0 no sum is ever -0 (the sign bit
+        // of L is the sign of the response)
+        P l = A::fma(A::w(kp, f, 0), R0, A::zero());
+        l = A::fma(A::w(kp, f, 1), R1, l);
+        l = A::fma(A::w(kp, f, 2), R2, l);
+        l = A::fma(A::w(kp, f, 3), R4, l);
+        l = A::fma(A::w(kp, f, 4), R5, l);
+        L_[f][c0] = A::fma(A::w(kp, f, 5), R8, l);
+      }
+    }
+    if constexpr (!kSrcZ) {
+      const P A3 = A::add(A::add(R0, R1), R2);
+      const P A5 = A::add(A::add(A::add(A3, R4), R5), R8);
+      Q Q3[2], Q5[2];
 #pragma unroll
-        for (int f = 0; f < 2; ++f) {
-          // exact partial sums; starting from +0 no sum is ever -0 (the sign bit
-          // of L is the sign of the response)
-          V l = A::w(kp, f, 0) * R0 + V(0);
-          l = l + A::w(kp, f, 1) * R1;
-          l = l + A::w(kp, f, 2) * R2;
-          l = l + A::w(kp, f, 3) * R4;
-          l = l + A::w(kp, f, 4) * R5;
-          L_[f][c0][j] = l + A::w(kp, f, 5) * R8;
-        }
+      for (int j = 0; j < 2; ++j) {
+        Q3[j] = c3_[m1][j] + c3_[c0][j] + c3_[p1][j];
+        Q5[j] = P5[j] + c5_[p1][j] + c5_[S][j];
       }
-      if constexpr (!kSrcZ) {
-        const V A3 = R0 + R1 + R2;
-        const V A5 = A3 + R4 + R5 + R8;
-        const Q Q3 = c3_[m1][j] + c3_[c0][j] + c3_[p1][j];
-        const Q Q5 = c5_[m2][j] + c5_[m1][j] + c5_[c0][j] + c5_[p1][j] + c5n[j];
-        S_[0][c0][j] = A::sdpass(kp, 0, A3, A5, Q3, Q5);
-        if (kSd2) S_[1][c0][j] = A::sdpass(kp, 1, A3, A5, Q3, Q5);
-      }
+      A::sdfail(kp, 0, A3, A5, Q3, Q5, S_[0][c0]);
+      if (kSd2) A::sdfail(kp, 1, A3, A5, Q3, Q5, S_[1][c0]);
     }
     // replicated borders for the L stage (reading R2)
     if constexpr (kChk) {
       if (c >= Hrel) {
 #pragma unroll
-        for (int f = 0; f < 2; ++f)
-#pragma unroll
-          for (int j = 0; j < 2; ++j) L_[f][c0][j] = L_[f][m1][j];
+        for (int f = 0; f < 2; ++f) L_[f][c0] = L_[f][m1];
       }
       if (border) {
         fix_cols(L_[0][c0]);
@@ -508,15 +623,8 @@ struct Strip {
       }
       if (c == -Y0rel) {
 #pragma unroll
-        for (int f = 0; f < 2; ++f)
-#pragma unroll
-          for (int j = 0; j < 2; ++j) L_[f][m1][j] = L_[f][c0][j];
+        for (int f = 0; f < 2; ++f) L_[f][m1] = L_[f][c0];
       }
-    }
-#pragma unroll
-    for (int f = 0; f < 2; ++f) {
-      LW_[f][c0] = __shfl_up_sync(kFull, L_[f][c0][1], 1);
-      LE_[f][c0] = __shfl_down_sync(kFull, L_[f][c0][0], 1);
     }
   }
 
@@ -526,20 +634,29 @@ struct Strip {
     constexpr int r = (S + 1) & 3, rn = S, rs = (S + 2) & 3;  // rows t-3, t-4, t-2
 #pragma unroll
     for (int f = 0; f < 2; ++f) {
-#pragma unroll
-      for (int jj = 0; jj < 2; ++jj) {
-        const int j = 1 - jj;
-        const V Lc = L_[f][r][j], Ln = L_[f][rn][j], Ls = L_[f][rs][j];
-        const V Lw = j > 0 ? L_[f][r][0] : LW_[f][r];
-        const V Le = j < 1 ? L_[f][r][1] : LE_[f][r];
-        put(acc_[5 * f + 0], A::bits(Lc));
-        put(acc_[5 * f + 1], A::bits(A::neg(Lc)));
-        put(acc_[5 * f + 2], A::bits(Lc + Le));
-        put(acc_[5 * f + 3], A::bits(Lc + Ls));
-        const V mx = A::max3(A::max3(Lw, Lc, Le), Ln, Ls);
-        const V mn = A::min3(A::min3(Lw, Lc, Le), Ln, Ls);
-        put(acc_[5 * f + 4], A::cfail(kp, f, mx, mn));
-      }
+      const P Lc = L_[f][r], Ln = L_[f][rn], Ls = L_[f][rs];
+      // west / east neighbours of the lane's columns 0 / 1: the neighbouring lanes'
+      const V Lw = __shfl_up_sync(kFull, A::hi(Lc), 1), Le = __shfl_down_sync(kFull, A::lo(Lc), 1);
+      const V c0v = A::lo(Lc), c1v = A::hi(Lc);
+      const P nL = A::neg(Lc);
+      const P sS = A::add(Lc, Ls);
+      const V sE0 = A::add1(c0v, c1v), sE1 = A::add1(c1v, Le);
+      const P mx = A::mk(A::max3(A::max3(Lw, c0v, c1v), A::lo(Ln), A::lo(Ls)),
+                         A::max3(A::max3(c0v, c1v, Le), A::hi(Ln), A::hi(Ls)));
+      const P mn = A::mk(A::min3(A::min3(Lw, c0v, c1v), A::lo(Ln), A::lo(Ls)),
+                         A::min3(A::min3(c0v, c1v, Le), A::hi(Ln), A::hi(Ls)));
+      const P cf = A::cfail(kp, f, mx, mn);
+      // column 1 first: bit 30 - 2r + j for row r, column j
+      put(acc_[5 * f + 0], A::bits(c1v));
+      put(acc_[5 * f + 0], A::bits(c0v));
+      put(acc_[5 * f + 1], A::bits(A::hi(nL)));
+      put(acc_[5 * f + 1], A::bits(A::lo(nL)));
+      put(acc_[5 * f + 2], A::bits(sE1));
+      put(acc_[5 * f + 2], A::bits(sE0));
+      put(acc_[5 * f + 3], A::bits(A::hi(sS)));
+      put(acc_[5 * f + 3], A::bits(A::lo(sS)));
+      put(acc_[5 * f + 4], A::bits(A::hi(cf)));
+      put(acc_[5 * f + 4], A::bits(A::lo(cf)));
     }
     if constexpr (kSrcZ) return;
     put(acc_[10], S_[0][r][1]);
@@ -577,8 +694,8 @@ struct Strip {
     uint32_t m = 0;
 #pragma unroll
     for (int f = 0; f < 2; ++f) {
-      const uint32_t sd = kSd2 ? blk(10 + f) : blk(10);
-      m |= crossings(f) & ~blk(5 * f + 4) & sd;
+      const uint32_t sdf = kSd2 ? blk(10 + f) : blk(10);  // standard-deviation test fails
+      m |= crossings(f) & ~(blk(5 * f + 4) | sdf);
     }
     return replicate(b, m, sw_[kMA][lane]);
   }
@@ -791,10 +908,18 @@ struct Strip {
     // bits of rows no output depends on.  Bit blocks span 16 rows (four
     // iterations); block b covers rows [Y0 - 3 + 16b, Y0 + 13 + 16b) and its
     // median is stored at the end of group b + 2.
-    load_row<0>(-8);
-    load_row<1>(-7);
-    load_row<2>(-6);
-    load_row<3>(-5);
+    if constexpr (kAsync) {
+      // rows -8 .. -2 into slots 0 .. 6 (slot of row t = t & 7); each step
+      // refills the slot read one step before with the row seven ahead
+#pragma unroll
+      for (int i = 0; i < kRingRows - 1; ++i) load_row_async(ring_h_ + 128u * i, i - 8);
+    } else {
+      load_row<0>(-8);
+      load_row<1>(-7);
+      load_row<2>(-6);
+      load_row<3>(-5);
+    }
+    const uint32_t ring0 = ring_h_;
     const int32_t bmax = static_cast<int32_t>((Y1 - Y0 + 2) / 16);
     // one more block of delay per extra median level and for the crossing-map source
     const int32_t iters = 4 * (bmax + (kp.nhmf < 2 ? 3 : 4) + (kSrcZ ? 1 : 0));
@@ -809,19 +934,34 @@ struct Strip {
           // schedule (four steps of two columns) without computing the steps
 #pragma unroll
           for (int i = 0; i < 12; ++i) acc_[i] <<= 8;
-          if ((k & 3) == 3 && !end_group(k >> 2)) return false;
+          if ((k & 3) == 3 && !end_group(k >> 2)) {
+            async_drain();
+            return false;
+          }
           continue;
         }
       }
-      // centre rows of this iteration: 4k - 2 .. 4k + 1 and loaded rows 4k + 4 ..
-      // 4k + 7 (relative to Y0); the fix-ups act only on a border strip, at image
-      // row 0 and past row H - 1, and loads clamp only outside [rlo, rhi]
+      // centre rows of this iteration: 4k - 2 .. 4k + 1 and loaded rows 4k + la ..
+      // 4k + 3 + la (relative to Y0; la = the load distance); the fix-ups act only
+      // on a border strip, at image row 0 and past row H - 1, and loads clamp only
+      // outside [rlo, rhi].  The unchecked body loads without clamping, so it may
+      // run only when every row it loads lies in [rlo, rhi].
+      constexpr int32_t la = kAsync ? kRingRows - 1 : 4;
       const bool chk = border || (4 * k - 2 <= -Y0rel && -Y0rel <= 4 * k + 1) || 4 * k + 1 >= Hrel ||
-                       4 * k + 4 < rlo || 4 * k + 7 > rhi;
+                       4 * k + la < rlo || 4 * k + 3 + la > rhi;
+      if constexpr (kAsync) {
+        // ring slots of this iteration's rows 4k .. 4k + 3: 4 (k & 1) + S
+        ring_h_ = ring0 + ((k & 1) ? 512u : 0u);
+        ring_o_ = ring0 + ((k & 1) ? 0u : 512u);
+      }
       if (chk) four_steps<true>(4 * k);
       else four_steps<false>(4 * k);
-      if ((k & 3) == 3 && !end_group(k >> 2)) return false;
+      if ((k & 3) == 3 && !end_group(k >> 2)) {
+        async_drain();
+        return false;
+      }
     }
+    async_drain();
     return true;
   }
 };
@@ -846,7 +986,7 @@ __device__ __forceinline__ uint8_t *unit_marker(const ImageView &v, int64_t ux, 
 
 // Per-warp shared words of the streaming path (the caller's kernel owns one
 // array of this type per CTA and passes the warp's slice).
-constexpr int kStripWords = 28;
+constexpr int kStripWords = 36;  // 28 block words + the 8-row input ring
 using StripWords = uint32_t[kWarpsPerCta][kStripWords][32];
 __device__ __forceinline__ uint32_t (*warp_words(StripWords &w))[32] { return w[(threadIdx.x >> 5) % kWarpsPerCta]; }
 
@@ -857,7 +997,9 @@ template <typename T, bool kF32Log, bool kPair, bool kSd2, bool kSrcZ, bool kTai
 __device__ __forceinline__ void fast_unit(const ImageView &v, const KParams &kp, int64_t ux, int64_t uy, int,
                                           int uh, uint32_t (*words)[32]) {
   constexpr int kMode = kF32Log ? st::kModeF32Log : st::kModeF32;
-  static_assert(st::Strip<T, kMode, kPair, kSd2, kSrcZ>::kWords == kStripWords, "shared word layout");
+  static_assert(st::Strip<T, kMode, kPair, kSd2, kSrcZ>::kWords + st::Strip<T, kMode, kPair, kSd2, kSrcZ>::kRingRows ==
+                    kStripWords,
+                "shared word layout");
   if (kp.fbound < 0) return;
   constexpr int uw = strip_width(kSrcZ);
   const int64_t X0 = ux * uw;
