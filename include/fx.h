@@ -189,6 +189,12 @@ typedef struct {
  * fx_extract's.  descs is a HOST array of n descriptors, validated like
  * fx_extract's arguments; the table is copied before the call returns.
  * Output masks must not overlap each other or any input.
+ * The plan holds two descriptor tables and two sets of queue counters and
+ * alternates between them, so two calls on one plan may run at the same time
+ * (for example on two streams); a third call waits on the host until the
+ * first one's replay has finished.  Calls on one plan must come from one host
+ * thread at a time.  The plan's device is made current for the call and the
+ * caller's current device is restored before it returns.
  * Errors: FX_ERR_INVALID_ARG (n < 1, n > max_images, bad descriptor),
  * FX_ERR_CUDA.
  */
@@ -265,20 +271,27 @@ fx_status fx_hybrid_median(const void *img, int64_t width, int64_t height, int64
 
 /*
  * Batched extraction for callers that cannot allocate device memory.  The
- * paper has no counterpart; this entry point exists for deployment.  It does
- * what fx_extract_batch does (same masks, byte for byte) without a plan: its
- * only scratch (descriptor table and tile-queue counter, about 8 KiB) is a
- * fixed array inside the library that every GPU loading libfx.so reserves
- * until process exit.  The call itself allocates nothing on host or device.
+ * paper has no counterpart; this entry point exists for deployment: services
+ * whose device memory all belongs to another allocator (a framework's caching
+ * pool, a fixed arena), real-time loops that forbid cudaMalloc after start-up
+ * (it can synchronise the device and fail under fragmentation), and plug-ins
+ * handed buffers but no right to allocate.  It does what fx_extract_batch
+ * does (same masks, byte for byte) without a plan: the descriptor table
+ * travels in the kernel's launch parameters, and its only scratch, the
+ * tile-queue counter, sits in a fixed 256-byte array inside the library that
+ * every GPU loading libfx.so reserves until process exit.  The call allocates
+ * nothing on host or device.
  *   params  NULL = fx_params_default(FX_U16, 0)
- *   descs   HOST array of n descriptors, validated like fx_extract's arguments
+ *   descs   HOST array of n descriptors, validated like fx_extract's
+ *           arguments; read before the call returns
  *   n       1 .. FX_NOALLOC_MAX_IMAGES; a larger n returns FX_ERR_BUDGET and
  *           launches nothing
  * The first call on a device looks up the scratch array's device address
  * (once per device, with that device current); make that first call before
- * any stream capture.  Every call on a device shares the one array and leaves
- * its contents behind (each call resets the queue counter itself), so calls
- * whose work overlaps on the GPU race: serialise them (one stream, or events).
+ * any stream capture.  Every call on a device shares the one counter, which
+ * keeps the last call's value (each call resets it to zero on its stream
+ * before its kernel), so calls whose work overlaps on the GPU race: serialise
+ * them (one stream, or events).
  * Errors: FX_ERR_INVALID_ARG, FX_ERR_RANGE, FX_ERR_BUDGET, FX_ERR_CUDA.
  */
 #define FX_NOALLOC_MAX_IMAGES 128

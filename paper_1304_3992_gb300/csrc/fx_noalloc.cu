@@ -31,29 +31,35 @@ struct NoAllocImage {
   int32_t pad;
 };
 
-struct NoAllocHeader {
-  unsigned long long counter;  // tile queue; reset to 0 by every call
+// The descriptor table travels as a kernel parameter: the launch copies it,
+// so the call needs no host staging buffer and no copy of its own.
+struct NoAllocTable {
   int64_t total_units;
   int32_t n;
-  int32_t pad[11];             // header padded to 64 bytes
+  int32_t pad;
+  NoAllocImage im[FX_NOALLOC_MAX_IMAGES];
 };
 
-constexpr int kTableOffset = 256;
-constexpr size_t kScratchBytes = kTableOffset + sizeof(NoAllocImage) * FX_NOALLOC_MAX_IMAGES;
-static_assert(sizeof(NoAllocHeader) <= kTableOffset, "header must fit before the table");
+// The kernel's parameters: the table and one KParams per pixel type (CUDA
+// allows 32764 bytes of kernel parameters).
+static_assert(sizeof(NoAllocTable) + 2 * sizeof(KParams) + 64 <= 32764, "kernel parameters too large");
 
-// The scratch of every fx_extract_batch_noalloc call on this device.  Host code
-// must not pass this name to a kernel or a copy: on the host it is only a
-// stand-in for the symbol; its device address comes from cudaGetSymbolAddress.
+// The scratch of every fx_extract_batch_noalloc call on a device: the
+// tile-queue counter, reset to zero by each call before its kernel runs.
+// Host code must not pass this name to a kernel or a copy: on the host it is
+// only a stand-in for the symbol; its device address comes from
+// cudaGetSymbolAddress.
+constexpr size_t kScratchBytes = 256;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
 constexpr int kMaxDevices = 64;
 std::mutex g_setup_mutex;
 void *g_scratch_addr[kMaxDevices];
+bool g_attr_set[kMaxDevices];
 
-// Device address of the scratch array on the current device, looked up once
-// per device.
-fx_status scratch_address(void **out) {
+// Per-device set-up, once per device with that device current: the scratch
+// array's device address and the kernel's dynamic shared-memory limit.
+fx_status setup_device(void **out) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return FX_ERR_CUDA;
   if (dev < 0 || dev >= kMaxDevices) return FX_ERR_UNSUPPORTED;
@@ -70,29 +76,27 @@ fx_status scratch_address(void **out) {
   return FX_OK;
 }
 
-// The persistent tile-queue loop of the batched path, reading its table and
-// counter from the scratch array passed in `scratch`.
-__global__ void __launch_bounds__(gen::NT) noalloc_batch_kernel(unsigned char *scratch, KParams kp8,
-                                                                 KParams kp16) {
+// The persistent tile-queue loop of the batched path: the table from the
+// kernel parameter, the queue counter from the scratch array.
+__global__ void __launch_bounds__(gen::NT) noalloc_batch_kernel(unsigned long long *counter,
+                                                                 const __grid_constant__ NoAllocTable tab,
+                                                                 const __grid_constant__ KParams kp8,
+                                                                 const __grid_constant__ KParams kp16) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ long long s_unit;
-  NoAllocHeader *hdr = reinterpret_cast<NoAllocHeader *>(scratch);
-  const NoAllocImage *ims = reinterpret_cast<const NoAllocImage *>(scratch + kTableOffset);
-  const long long total = hdr->total_units;
-  const int n = hdr->n;
   for (;;) {
-    if (threadIdx.x == 0) s_unit = static_cast<long long>(atomicAdd(&hdr->counter, 1ULL));
+    if (threadIdx.x == 0) s_unit = static_cast<long long>(atomicAdd(counter, 1ULL));
     __syncthreads();
     const long long u = s_unit;
     __syncthreads();
-    if (u >= total) break;
-    int lo = 0, hi = n - 1;
+    if (u >= tab.total_units) break;
+    int lo = 0, hi = tab.n - 1;
     while (lo < hi) {
       int mid = (lo + hi + 1) >> 1;
-      if (ims[mid].unit_begin <= u) lo = mid;
+      if (tab.im[mid].unit_begin <= u) lo = mid;
       else hi = mid - 1;
     }
-    const NoAllocImage &b = ims[lo];
+    const NoAllocImage &b = tab.im[lo];
     const long long local = u - b.unit_begin;
     ImageView v{b.img, b.width, b.height, b.pitch, 0, b.elem, b.out, b.out_pitch, 0, b.height, b.height};
     const int64_t ux = local % b.units_x, uy = local / b.units_x;
@@ -125,11 +129,10 @@ extern "C" fx_status fx_extract_batch_noalloc(const fx_params *params, const fx_
   const fx_status st16 = make_kparams(params, 65535, &kp16);
   if (st16 != FX_OK) kp16 = kp8;
 
-  // The table is built on the host stack and copied into the scratch array.
-  unsigned char table[kScratchBytes];
-  std::memset(table, 0, sizeof(table));
-  NoAllocHeader *hdr = reinterpret_cast<NoAllocHeader *>(table);
-  NoAllocImage *ims = reinterpret_cast<NoAllocImage *>(table + kTableOffset);
+  // The table is filled on the host stack and handed to the launch by value.
+  static_assert(sizeof(NoAllocTable) <= 16384, "table on the stack");
+  NoAllocTable tab;
+  std::memset(&tab, 0, sizeof(tab));
   int64_t total = 0;
   for (int32_t i = 0; i < n; ++i) {
     const fx_image_desc &d = descs[i];
@@ -137,7 +140,7 @@ extern "C" fx_status fx_extract_batch_noalloc(const fx_params *params, const fx_
     st = check_image(d.img, d.width, d.height, d.pitch_bytes, d.dtype, d.out_mask, op);
     if (st != FX_OK) return st;
     if (d.dtype == FX_U16 && st16 != FX_OK) return st16;
-    NoAllocImage &b = ims[i];
+    NoAllocImage &b = tab.im[i];
     b.img = d.img;
     b.width = d.width;
     b.height = d.height;
@@ -152,20 +155,19 @@ extern "C" fx_status fx_extract_batch_noalloc(const fx_params *params, const fx_
   for (int32_t i = 0; i < n; ++i)
     for (int32_t j = 0; j < n; ++j) {
       if (i == j) continue;
-      const uintptr_t o0 = reinterpret_cast<uintptr_t>(ims[i].out);
-      const uintptr_t o1 = o0 + (ims[i].height - 1) * ims[i].out_pitch + ims[i].width;
-      const uintptr_t p0 = reinterpret_cast<uintptr_t>(ims[j].out);
-      const uintptr_t p1 = p0 + (ims[j].height - 1) * ims[j].out_pitch + ims[j].width;
-      const uintptr_t q0 = reinterpret_cast<uintptr_t>(ims[j].img);
-      const uintptr_t q1 = q0 + (ims[j].height - 1) * ims[j].pitch + ims[j].width * ims[j].elem;
+      const uintptr_t o0 = reinterpret_cast<uintptr_t>(tab.im[i].out);
+      const uintptr_t o1 = o0 + (tab.im[i].height - 1) * tab.im[i].out_pitch + tab.im[i].width;
+      const uintptr_t p0 = reinterpret_cast<uintptr_t>(tab.im[j].out);
+      const uintptr_t p1 = p0 + (tab.im[j].height - 1) * tab.im[j].out_pitch + tab.im[j].width;
+      const uintptr_t q0 = reinterpret_cast<uintptr_t>(tab.im[j].img);
+      const uintptr_t q1 = q0 + (tab.im[j].height - 1) * tab.im[j].pitch + tab.im[j].width * tab.im[j].elem;
       if ((j > i && overlaps(o0, o1, p0, p1)) || overlaps(o0, o1, q0, q1)) return FX_ERR_INVALID_ARG;
     }
-  hdr->counter = 0;
-  hdr->total_units = total;
-  hdr->n = n;
+  tab.total_units = total;
+  tab.n = n;
 
   void *scratch = nullptr;
-  if ((st = scratch_address(&scratch)) != FX_OK) return st;
+  if ((st = setup_device(&scratch)) != FX_OK) return st;
   int dev = 0, sms = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
@@ -173,15 +175,18 @@ extern "C" fx_status fx_extract_batch_noalloc(const fx_params *params, const fx_
   const size_t smem = gen::general_smem_bytes(kp8) > gen::general_smem_bytes(kp16)
                           ? gen::general_smem_bytes(kp8)
                           : gen::general_smem_bytes(kp16);
-  if (cudaFuncSetAttribute(noalloc_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           static_cast<int>(smem)) != cudaSuccess)
-    return FX_ERR_CUDA;
+  {
+    std::lock_guard<std::mutex> lock(g_setup_mutex);
+    if (!g_attr_set[dev]) {  // the largest dynamic shared memory any parameter set needs
+      if (cudaFuncSetAttribute(noalloc_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) !=
+          cudaSuccess)
+        return FX_ERR_CUDA;
+      g_attr_set[dev] = true;
+    }
+  }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  // Header (with the counter at zero) and descriptors in one copy; the copy
-  // reads the stack table before this call returns (pageable source).
-  const size_t bytes = kTableOffset + sizeof(NoAllocImage) * static_cast<size_t>(n);
-  if (cudaMemcpyAsync(scratch, table, bytes, cudaMemcpyHostToDevice, s) != cudaSuccess) return FX_ERR_CUDA;
-  noalloc_batch_kernel<<<static_cast<unsigned>(sms * 2), gen::NT, smem, s>>>(
-      static_cast<unsigned char *>(scratch), kp8, kp16);
+  unsigned long long *counter = static_cast<unsigned long long *>(scratch);
+  if (cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s) != cudaSuccess) return FX_ERR_CUDA;
+  noalloc_batch_kernel<<<static_cast<unsigned>(sms * 2), gen::NT, smem, s>>>(counter, tab, kp8, kp16);
   return cudaGetLastError() == cudaSuccess ? FX_OK : FX_ERR_CUDA;
 }

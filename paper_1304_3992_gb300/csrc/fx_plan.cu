@@ -199,12 +199,14 @@ struct fx_plan {
   fx_status st16;  // FX_ERR_RANGE when 16-bit images cannot be evaluated exactly
   bool fast;
   int device, max_images, num_sms;
-  // batch workspace
-  unsigned char *d_table;
+  // batch workspace, double-buffered: graph i copies host table i into device
+  // table i and runs on queue counters i, so two replays (e.g. from two
+  // streams) can be in flight; a third waits on the host for the first
+  unsigned char *d_table[2];
   unsigned char *h_table[2];
   cudaEvent_t h_free[2];
   int h_next;
-  unsigned long long *d_counter;
+  unsigned long long *d_counter[2];
   int *d_status;
   cudaGraphExec_t graph[2];
   int unit_w, unit_h, ctas_per_sm;
@@ -220,6 +222,20 @@ struct fx_plan {
 };
 
 namespace {
+
+// Makes the plan's device current for one entry point and restores the
+// caller's current device on return.
+struct DeviceScope {
+  int prev = -1;
+  bool ok = false;
+  explicit DeviceScope(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    ok = cudaSetDevice(dev) == cudaSuccess;
+  }
+  ~DeviceScope() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
 
 void destroy_graphs(fx_plan *p) {
   for (int i = 0; i < 2; ++i)
@@ -251,19 +267,19 @@ fx_status build_graph(fx_plan *p, int i) {
   cudaMemcpy3DParms cp;
   std::memset(&cp, 0, sizeof cp);
   cp.srcPtr = make_cudaPitchedPtr(p->h_table[i], table_bytes(p->max_images), table_bytes(p->max_images), 1);
-  cp.dstPtr = make_cudaPitchedPtr(p->d_table, table_bytes(p->max_images), table_bytes(p->max_images), 1);
+  cp.dstPtr = make_cudaPitchedPtr(p->d_table[i], table_bytes(p->max_images), table_bytes(p->max_images), 1);
   cp.extent = make_cudaExtent(table_bytes(p->max_images), 1, 1);
   cp.kind = cudaMemcpyHostToDevice;
   cudaMemsetParams ms;
   std::memset(&ms, 0, sizeof ms);
-  ms.dst = p->d_counter;
+  ms.dst = p->d_counter[i];
   ms.value = 0;
   ms.elementSize = 4;
   ms.width = 2 * kGroups;  // the queue counters
   ms.height = 1;
   ms.pitch = 8 * kGroups;
-  const unsigned char *tab = p->d_table;
-  unsigned long long *ctr = p->d_counter;
+  const unsigned char *tab = p->d_table[i];
+  unsigned long long *ctr = p->d_counter[i];
   int *stp = p->d_status;
   KParams k8 = p->kp8, k16 = p->kp16;
   void *args[] = {&tab, &ctr, &stp, &k8, &k16};
@@ -345,8 +361,10 @@ fx_status fill_table(fx_plan *p, unsigned char *h, const fx_image_desc *d, int32
   for (int32_t i = 0; i < n; ++i) {
     const int64_t op = d[i].out_pitch ? d[i].out_pitch : d[i].width;
     const int64_t elem = d[i].dtype == FX_U8 ? 1 : 2;
+    // the load-path rule of pair_loads_ok (fx_stream.cu)
     const bool pair = p->fast && reinterpret_cast<uintptr_t>(d[i].img) % (2 * elem) == 0 &&
-                      d[i].pitch_bytes % (2 * elem) == 0 && d[i].width % 2 == 0;
+                      d[i].pitch_bytes % (2 * elem) == 0 &&
+                      (d[i].width % 2 == 0 || d[i].pitch_bytes >= (d[i].width + 1) * elem);
     if (p->fast && group_of(pair, static_cast<int>(elem)) != pass) continue;
     fx_status st = check_image(d[i].img, d[i].width, d[i].height, d[i].pitch_bytes, d[i].dtype,
                                d[i].out_mask, op);
@@ -429,15 +447,16 @@ fx_status fx_plan_create(fx_plan **out, const fx_params *params, int32_t max_ima
   p->unit_h = kDefaultUnitH;
   p->ctas_per_sm = p->fast ? kFirstPassCtas : 2;
   p->auto_h = true;
-  if (cudaSetDevice(device) != cudaSuccess || cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
+  DeviceScope dev(device);
+  if (!dev.ok || cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
     delete p;
     return FX_ERR_CUDA;
   }
-  bool ok = cudaMalloc(&p->d_table, table_bytes(max_images)) == cudaSuccess &&
-            cudaMalloc(&p->d_counter, 8 * kGroups) == cudaSuccess && cudaMalloc(&p->d_status, 4) == cudaSuccess &&
-            cudaMemset(p->d_status, 0, 4) == cudaSuccess;
+  bool ok = cudaMalloc(&p->d_status, 4) == cudaSuccess && cudaMemset(p->d_status, 0, 4) == cudaSuccess;
   for (int i = 0; i < 2 && ok; ++i) {
-    ok = cudaMallocHost(&p->h_table[i], table_bytes(max_images)) == cudaSuccess &&
+    ok = cudaMalloc(&p->d_table[i], table_bytes(max_images)) == cudaSuccess &&
+         cudaMalloc(&p->d_counter[i], 8 * kGroups) == cudaSuccess &&
+         cudaMallocHost(&p->h_table[i], table_bytes(max_images)) == cudaSuccess &&
          cudaEventCreateWithFlags(&p->h_free[i], cudaEventDisableTiming) == cudaSuccess;
     if (ok) std::memset(p->h_table[i], 0, table_bytes(max_images));
   }
@@ -458,7 +477,7 @@ fx_status fx_plan_create(fx_plan **out, const fx_params *params, int32_t max_ima
 
 fx_status fx_plan_destroy(fx_plan *p) {
   if (!p) return FX_ERR_INVALID_ARG;
-  cudaSetDevice(p->device);
+  DeviceScope dev(p->device);
   for (int i = 0; i < 2; ++i)
     if (p->h_free[i]) cudaEventSynchronize(p->h_free[i]);
   if (p->s_h2d) cudaStreamSynchronize(p->s_h2d);
@@ -475,8 +494,10 @@ fx_status fx_plan_destroy(fx_plan *p) {
     if (p->ev_comp[i]) cudaEventDestroy(p->ev_comp[i]);
     if (p->ev_out[i]) cudaEventDestroy(p->ev_out[i]);
   }
-  if (p->d_table) cudaFree(p->d_table);
-  if (p->d_counter) cudaFree(p->d_counter);
+  for (int i = 0; i < 2; ++i) {
+    if (p->d_table[i]) cudaFree(p->d_table[i]);
+    if (p->d_counter[i]) cudaFree(p->d_counter[i]);
+  }
   if (p->d_status) cudaFree(p->d_status);
   if (p->s_h2d) cudaStreamDestroy(p->s_h2d);
   if (p->s_comp) cudaStreamDestroy(p->s_comp);
@@ -487,7 +508,8 @@ fx_status fx_plan_destroy(fx_plan *p) {
 
 fx_status fx_extract_batch(fx_plan *p, const fx_image_desc *descs, int32_t n, void *stream) {
   if (!p || !descs || n < 1 || n > p->max_images) return FX_ERR_INVALID_ARG;
-  if (cudaSetDevice(p->device) != cudaSuccess) return FX_ERR_CUDA;
+  DeviceScope dev(p->device);
+  if (!dev.ok) return FX_ERR_CUDA;
   const int i = p->h_next;
   // the previous replay that read host table i must have copied it out
   if (cudaEventSynchronize(p->h_free[i]) != cudaSuccess) return FX_ERR_CUDA;
@@ -505,7 +527,8 @@ fx_status fx_plan_set_tile(fx_plan *p, int32_t tile_w, int32_t tile_h, int32_t c
   // tile_h 0: the height is picked per batch (the wave model in fill_table)
   const bool automatic = tile_h == 0;
   if (!fast_unit_shape_ok(tile_w, automatic ? kDefaultUnitH : tile_h, p->kp8.source == 1)) return FX_ERR_INVALID_ARG;
-  if (cudaSetDevice(p->device) != cudaSuccess) return FX_ERR_CUDA;
+  DeviceScope dev(p->device);
+  if (!dev.ok) return FX_ERR_CUDA;
   for (int i = 0; i < 2; ++i)
     if (cudaEventSynchronize(p->h_free[i]) != cudaSuccess) return FX_ERR_CUDA;
   p->unit_w = tile_w;
@@ -518,6 +541,8 @@ fx_status fx_plan_set_tile(fx_plan *p, int32_t tile_w, int32_t tile_h, int32_t c
 fx_status fx_plan_autotune(fx_plan *p, const fx_image_desc *descs, int32_t n, void *stream,
                            int32_t *tile_w, int32_t *tile_h, int32_t *ctas_per_sm) {
   if (!p || !descs || n < 1 || n > p->max_images) return FX_ERR_INVALID_ARG;
+  DeviceScope dev(p->device);
+  if (!dev.ok) return FX_ERR_CUDA;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return FX_ERR_CUDA;
@@ -564,7 +589,8 @@ fx_status fx_plan_autotune(fx_plan *p, const fx_image_desc *descs, int32_t n, vo
 
 fx_status fx_get_device_status(fx_plan *p, void *stream) {
   if (!p) return FX_ERR_INVALID_ARG;
-  if (cudaSetDevice(p->device) != cudaSuccess) return FX_ERR_CUDA;
+  DeviceScope dev(p->device);
+  if (!dev.ok) return FX_ERR_CUDA;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   int h = 0;
   if (cudaMemcpyAsync(&h, p->d_status, 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
@@ -598,7 +624,8 @@ int64_t chunk_rows(const HostJob &j) {
 // All chunks of all images through the slot ring: the copy-in of a chunk, the
 // kernel of the one before and the copy-out of the one before that overlap.
 fx_status host_pipeline(fx_plan *p, const HostJob *jobs, int32_t n) {
-  if (cudaSetDevice(p->device) != cudaSuccess) return FX_ERR_CUDA;
+  DeviceScope dev(p->device);
+  if (!dev.ok) return FX_ERR_CUDA;
   size_t need_in = 0, need_out = 0;
   for (int32_t i = 0; i < n; ++i) {
     const KParams &kp = jobs[i].elem == 1 ? p->kp8 : p->kp16;

@@ -62,10 +62,15 @@ cudaError_t launch_t(const ImageView &v, const KParams &kp, cudaStream_t s, int6
 bool fast_path_supported(const KParams &kp) { return kp.nhmf <= 1 || (kp.nhmf == 2 && kp.r_m <= 3); }
 
 // One aligned load per lane and row: base and pitch multiples of two pixels,
-// even width (so every lane's clamped columns lie in one aligned pair).
+// and an even width or a row pitch with room for one more pixel, so that
+// every lane's clamped columns lie in one aligned pair (for an odd width the
+// last column's pair also holds the first padding element, which is never
+// used; the pair is one aligned load that contains an image element, so it
+// stays within the page of that element).
 bool pair_loads_ok(const ImageView &v) {
   const int64_t two = 2 * static_cast<int64_t>(v.elem);
-  return reinterpret_cast<uintptr_t>(v.img) % two == 0 && v.pitch % two == 0 && v.width % 2 == 0;
+  return reinterpret_cast<uintptr_t>(v.img) % two == 0 && v.pitch % two == 0 &&
+         (v.width % 2 == 0 || v.pitch >= (v.width + 1) * v.elem);
 }
 
 // Resident warps of the streaming kernel on the current device (3 CTAs of 4

@@ -316,6 +316,7 @@ struct Strip {
   uint32_t S_[2][4][2];  // sign bit: the standard-deviation test fails
   uint32_t raw_[4], raw1_[4];  // loaded pixels of rows t..t+3 (raw1_: second pixel, !kPair)
   uint32_t vmax_;
+  uint32_t vhi_;  // 0 when the high half of this lane's loaded pair is padding (odd width)
   uint32_t acc_[12];
   // Words of earlier blocks, touched once per 16 rows, live in shared memory:
   // kBlk.. = previous block (12 words), kPneg / kPpos / kPsS = neg / pos / sS of
@@ -376,9 +377,14 @@ struct Strip {
     pitch32 = static_cast<uint32_t>(v.pitch);
     const unsigned char *base = static_cast<const unsigned char *>(v.img) + (Y0 + rbase - v.row0) * v.pitch;
     const int64_t d0 = x < 0 ? 0 : (x >= W ? W - 1 : x), d1 = x + 1 < 0 ? 0 : (x + 1 >= W ? W - 1 : x + 1);
+    vhi_ = 0xFFFFu;
     if constexpr (kPair) {
-      // the even pair (cb, cb + 1) inside the row that holds both clamped columns
-      const int64_t cb = (d0 < W - 2 ? d0 : W - 2) & ~int64_t{1};
+      // the even pair (cb, cb + 1) inside the row that holds both clamped
+      // columns; for an odd width the last column's pair is (W - 1, W), W being
+      // the first padding element of the row
+      const int64_t we = W + (W & 1);
+      const int64_t cb = (d0 < we - 2 ? d0 : we - 2) & ~int64_t{1};
+      if (cb + 1 >= W) vhi_ = 0;
       p0_ = p1_ = base + cb * static_cast<int64_t>(sizeof(T));
       const uint32_t h0 = static_cast<uint32_t>(d0 - cb), h1 = static_cast<uint32_t>(d1 - cb);
       if constexpr (sizeof(T) == 2) {
@@ -839,7 +845,7 @@ struct Strip {
   // End of the 16 steps of group g: block g is packed in acc_.
   __device__ __forceinline__ bool end_group(int64_t g) {
     if (check) {
-      const uint32_t m = max(vmax_ & 0xFFFFu, vmax_ >> 16);
+      const uint32_t m = max(vmax_ & 0xFFFFu, (vmax_ >> 16) & vhi_);
       if (__any_sync(kFull, m > static_cast<uint32_t>(kp.fbound))) return false;
     }
     uint32_t m = 0;

@@ -1,4 +1,6 @@
 // fx_tile.cu -- grid launch of the general fused extraction tile (fx_tile.cuh).
+#include <atomic>
+
 #include "fx_tile.cuh"
 
 namespace fx {
@@ -15,15 +17,21 @@ __global__ void __launch_bounds__(NT) tile_general_kernel(ImageView v, KParams k
   gen::general_tile<T>(v, kp, tx * TW, v.y_begin + ty * TH, smem);
 }
 
+// The kernel's dynamic shared-memory limit is a per-device attribute: set it
+// once on every device the process launches it on.
+constexpr int kMaxDevices = 64;
+
 template <typename T>
 cudaError_t launch_t(const ImageView &v, const KParams &kp, cudaStream_t s) {
   size_t smem = gen::general_smem_bytes(kp);
-  static bool attr_set = false;  // per template instance; benign race (idempotent)
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(tile_general_kernel<T>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+  static std::atomic<bool> attr_set[kMaxDevices];  // per template instance and device (idempotent)
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices || !attr_set[dev].load(std::memory_order_acquire)) {
+    e = cudaFuncSetAttribute(tile_general_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
     if (e != cudaSuccess) return e;
-    attr_set = true;
+    if (dev >= 0 && dev < kMaxDevices) attr_set[dev].store(true, std::memory_order_release);
   }
   int64_t tiles_x = (v.width + TW - 1) / TW;
   int64_t tiles_y = (v.y_end - v.y_begin + TH - 1) / TH;

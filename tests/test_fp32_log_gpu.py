@@ -149,9 +149,15 @@ def test_fp32_ms8192_sampled_rows(cuda_lib):
         assert tolerance.compare_with_oracle(img, got[y0:y1], d, rows=(y0, y1)) == 0
 
 
-def test_fp32_band16384_sampled_rows(cuda_lib):
-    band = next(scenes.ms_bands_u16_12bit(bands=[2]))
+def test_fp32_band16384_unit_seams_all_bands(cuda_lib):
+    """The four 16384^2 bands in the FP32-LoG mode: 40-row bands across the
+    first three unit seams, the top and bottom rows and one random band, under
+    the parity rule (zero differing pixels expected)."""
+    import fullsize
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    uh = fullsize.unit_height(16384, 16384, sms)
     d, p = pair(16.0)
-    got = run(cuda_lib, band, p)
-    for y0, y1 in _sample_rows(band.shape[0], 4, 6, 5):
-        assert tolerance.compare_with_oracle(band, got[y0:y1], d, rows=(y0, y1)) == 0
+    for b, band in enumerate(scenes.ms_bands_u16_12bit()):
+        got = run(cuda_lib, band, p)
+        for y0, y1 in fullsize.seam_bands(band.shape[0], uh, seed=10 + b):
+            assert tolerance.compare_with_oracle(band, got[y0:y1], d, rows=(y0, y1)) == 0, f"band {b} rows {y0}:{y1}"

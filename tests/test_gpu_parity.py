@@ -95,6 +95,31 @@ def test_pitched_rows(cuda_lib, pitch_extra):
     assert_same(got, oracle.extract(img, d), f"pitch {pitch}")
 
 
+@pytest.mark.parametrize("bits", [8, 12, 16])
+def test_odd_width_pair_and_fallback_loads(cuda_lib, bits):
+    """Odd widths: with exactly width * elem bytes per row every lane loads its
+    two pixels one by one; with room for one more pixel per row the last
+    column is loaded as the aligned pair (W - 1, W), W being padding.  The
+    padding holds the largest value of the type, which must neither reach the
+    mask nor send the strip to the integer pass.  Both layouts against the
+    oracle, on images taller than one work unit."""
+    from paper_1304_3992_gb300 import fx
+    for (h, w) in [(901, 333), (257, 1001), (64, 53)]:
+        img = scenes.scene(w, h, seed=h + w + bits, n_rects=max(1, h * w // 500),
+                           noise_sigma=4.0 * (1 << (bits - 8)), impulse_frac=0.005, bits=bits)
+        scale = float(1 << (bits - 8)) if bits <= 12 else 16.0
+        d, p = pair(scale, fx.FX_U8 if bits == 8 else fx.FX_U16)
+        ref = oracle.extract(img, d)
+        assert_same(run(cuda_lib, img, p), ref, f"{h}x{w} contiguous")
+        elem = img.itemsize
+        for pitch in ((w + 1) * elem if ((w + 1) * elem) % (2 * elem) == 0 else (w + 2) * elem,
+                      ((w * elem + 255) // 256) * 256):
+            top = 255 if elem == 1 else 65535
+            buf = torch.full((h, pitch // elem), top, dtype=torch.uint8 if elem == 1 else torch.uint16, device="cuda")
+            buf[:, :w] = dev(img)
+            assert_same(run(cuda_lib, buf[:, :w], p), ref, f"{h}x{w} pitch {pitch}")
+
+
 def test_pitched_output(cuda_lib):
     img = scenes.scene(150, 60, seed=4, n_rects=8, noise_sigma=4, impulse_frac=0.01, bits=8)
     d, p = pair(1.0)
@@ -175,12 +200,78 @@ def test_ms8192_u16_sampled_rows(cuda_lib):
     assert_same(got[3000:3100, :], oracle.extract(img, d, rows=(3000, 3100)), "rows 3000:3100")
 
 
-def test_band16384_u16_sampled_rows(cuda_lib):
-    band = next(scenes.ms_bands_u16_12bit(bands=[1]))
+def test_band16384_u16_unit_seams_all_bands(cuda_lib):
+    """The benchmark's four 16384^2 12-bit bands, each in the benchmark's
+    launch configuration: 40-row bands across the first three unit seams (720
+    rows apart on 152 SMs), the top and bottom rows and one random band,
+    against the oracle."""
+    import fullsize
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    uh = fullsize.unit_height(16384, 16384, sms)
+    if sms == 152:
+        assert uh == 720
     d, p = pair(16.0)
-    got = run(cuda_lib, band, p)
-    for y0, y1 in _sample_bands(band.shape[0], 4, 8, 2):
-        assert_same(got[y0:y1], oracle.extract(band, d, rows=(y0, y1)), f"rows {y0}:{y1}")
+    for b, band in enumerate(scenes.ms_bands_u16_12bit()):
+        got = run(cuda_lib, band, p)
+        for y0, y1 in fullsize.seam_bands(band.shape[0], uh, seed=b):
+            assert_same(got[y0:y1], oracle.extract(band, d, rows=(y0, y1)), f"band {b} rows {y0}:{y1}")
+
+
+def test_config4_batch_full_size_sampled(cuda_lib):
+    """The 64 uneven scenes of the batched workload at full size (sides 1000 to
+    12000, uint8 and 12-bit uint16, pitch rounded to 256 B) in one batched call;
+    sampled row bands of four uint16 scenes (12-bit thresholds) and, from a
+    second call with 8-bit thresholds, of four uint8 scenes against the
+    oracle, and every scene's mask against its single-image call on a band."""
+    batch = scenes.uneven_batch(n=64)
+    imgs = [dev_pitched(view, view.strides[0]) for view, _ in batch]
+    outs = [torch.full(view.shape, 9, dtype=torch.uint8, device="cuda") for view, _ in batch]
+    rng = np.random.default_rng(64)
+    for scale, dt, picks in ((16.0, np.uint16, (1, 3, 21, 63)), (1.0, np.uint8, (0, 2, 30, 62))):
+        d, p = pair(scale)
+        with cuda_lib.Plan(p, max_images=64) as plan:
+            plan.extract_batch(list(zip(imgs, outs)))
+            torch.cuda.synchronize()
+            assert plan.device_status() == 0
+        feats = 0
+        for i in picks:
+            view = batch[i][0]
+            assert view.dtype == dt
+            H = view.shape[0]
+            y = int(rng.integers(16, H - 40))
+            got = outs[i].cpu().numpy()
+            for y0, y1 in ((0, 16), (y, y + 24), (H - 16, H)):
+                ref = oracle.extract(view, d, rows=(y0, y1))
+                assert_same(got[y0:y1], ref, f"scene {i} rows {y0}:{y1}")
+                feats += int(ref.sum())
+        assert feats > 0
+        for i in range(0, 64, 7):  # batched output equals the single-image call
+            single = cuda_lib.extract(imgs[i], p)
+            torch.cuda.synchronize()
+            assert torch.equal(single, outs[i]), f"scene {i}"
+
+
+def test_batch_two_streams_one_plan(cuda_lib):
+    """Two calls on one plan from two streams run without waiting for each
+    other (the plan alternates between two descriptor tables and two sets of
+    queue counters); both give the single-image masks."""
+    batch = scenes.uneven_batch(n=12, lo=200, hi=1500, seed=12, master_side=1600)
+    d, p = pair(16.0)
+    pairs = [(dev_pitched(v, v.strides[0]), torch.full(v.shape, 9, dtype=torch.uint8, device="cuda"))
+             for v, _ in batch]
+    singles = [run(cuda_lib, img, p) for img, _ in pairs]
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    with cuda_lib.Plan(p, max_images=8) as plan:
+        for rep in range(3):
+            for _, o in pairs:
+                o.fill_(9)
+            torch.cuda.synchronize()
+            plan.extract_batch(pairs[:6], stream=s1)
+            plan.extract_batch(pairs[6:], stream=s2)
+            torch.cuda.synchronize()
+            for i, ((_, out), single) in enumerate(zip(pairs, singles)):
+                assert_same(out.cpu().numpy(), single, f"rep {rep} image {i}")
+        assert plan.device_status() == 0
 
 
 def test_batch_matches_single_and_oracle(cuda_lib):

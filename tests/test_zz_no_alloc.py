@@ -39,17 +39,26 @@ def _noalloc(fx, params, pairs):
 
 
 def test_noalloc_matches_fx_extract_twice(cuda_lib):
+    """Calls in a row (the scratch keeps the previous call's counter) give the
+    masks of fx_extract.  The 12-bit thresholds exercise the uint16 images, the
+    8-bit thresholds of the last call the uint8 ones (their masks are empty
+    under 12-bit thresholds), so each pixel type is compared on masks with
+    feature pixels."""
     fx = cuda_lib
-    p = fx.make_params(fx.FX_U16, 12)
-    for call, (seed, n) in enumerate(((3, 9), (4, 5))):
+    p12 = fx.make_params(fx.FX_U16, 12)
+    p8 = fx.make_params(fx.FX_U8, 8)
+    features = {1: 0, 2: 0}
+    for call, (seed, n, p, elem) in enumerate(((3, 9, p12, 2), (4, 5, p12, 2), (5, 7, p8, 1))):
         pairs = _images(seed, n)
         singles = [fx.extract(img, p).cpu().numpy() for img, _ in pairs]
         assert _noalloc(fx, p, pairs) == 0
         torch.cuda.synchronize()
-        for i, ((_, out), ref) in enumerate(zip(pairs, singles)):
+        for i, ((img, out), ref) in enumerate(zip(pairs, singles)):
             got = out.cpu().numpy()
             assert np.array_equal(got, ref), f"call {call} image {i}: {int((got != ref).sum())} bytes differ"
-        assert sum(int(r.sum()) for r in singles) > 0
+            if img.element_size() == elem:
+                features[elem] += int(ref.sum())
+    assert features[1] > 0 and features[2] > 0, features
 
 
 def test_noalloc_rejects_oversized_batch(cuda_lib):
