@@ -291,6 +291,7 @@ fx_status fx_log_mask_fp32(double sigma, int32_t mask_q, float w[25]) {
 
 fx_status fx_extract(const void *img, int64_t width, int64_t height, int64_t pitch_bytes,
                      fx_dtype dtype, const fx_params *params, uint8_t *out_mask, void *stream) {
+  NvtxRange range("fx_extract");
   fx_params def;
   if (!params) {
     fx_params_default(&def, dtype, 0);

@@ -274,6 +274,7 @@ using namespace fx;
 extern "C" fx_status fx_hybrid_median(const void *img, int64_t width, int64_t height, int64_t pitch_bytes,
                                       fx_dtype dtype, int32_t window, void *out, int64_t out_pitch_bytes,
                                       void *stream) {
+  NvtxRange range("fx_hybrid_median");
   if (window != 3 && window != 5) return FX_ERR_INVALID_ARG;
   if (!img || !out || (dtype != FX_U8 && dtype != FX_U16)) return FX_ERR_INVALID_ARG;
   const int64_t elem = dtype == FX_U8 ? 1 : 2;

@@ -3,6 +3,7 @@
 
 #include <cstdint>
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "../../include/fx.h"
 
@@ -56,6 +57,15 @@ struct KParams {
   // t_sdmax, [20..23] lo and [24..27] hi of the 3x3 test.  An empty interval
   // has lo above every count.
   uint32_t zsel[2][28];
+};
+
+// NVTX range over a host-side scope (launches, copies, pipeline stages); the
+// ranges cost nothing unless a profiler is attached.
+struct NvtxRange {
+  explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange &) = delete;
+  NvtxRange &operator=(const NvtxRange &) = delete;
 };
 
 // Derive KParams from fx_params for images whose values are <= maxval.

@@ -115,6 +115,7 @@ using namespace fx;
 
 extern "C" fx_status fx_extract_batch_noalloc(const fx_params *params, const fx_image_desc *descs,
                                               int32_t n, void *stream) {
+  NvtxRange range("fx_extract_batch_noalloc");
   if (!descs || n < 1) return FX_ERR_INVALID_ARG;
   if (n > FX_NOALLOC_MAX_IMAGES) return FX_ERR_BUDGET;
   fx_params def;

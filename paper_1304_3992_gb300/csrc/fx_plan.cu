@@ -507,6 +507,7 @@ fx_status fx_plan_destroy(fx_plan *p) {
 }
 
 fx_status fx_extract_batch(fx_plan *p, const fx_image_desc *descs, int32_t n, void *stream) {
+  NvtxRange range("fx_extract_batch");
   if (!p || !descs || n < 1 || n > p->max_images) return FX_ERR_INVALID_ARG;
   DeviceScope dev(p->device);
   if (!dev.ok) return FX_ERR_CUDA;
@@ -540,6 +541,7 @@ fx_status fx_plan_set_tile(fx_plan *p, int32_t tile_w, int32_t tile_h, int32_t c
 
 fx_status fx_plan_autotune(fx_plan *p, const fx_image_desc *descs, int32_t n, void *stream,
                            int32_t *tile_w, int32_t *tile_h, int32_t *ctas_per_sm) {
+  NvtxRange range("fx_plan_autotune");
   if (!p || !descs || n < 1 || n > p->max_images) return FX_ERR_INVALID_ARG;
   DeviceScope dev(p->device);
   if (!dev.ok) return FX_ERR_CUDA;
@@ -624,6 +626,7 @@ int64_t chunk_rows(const HostJob &j) {
 // All chunks of all images through the slot ring: the copy-in of a chunk, the
 // kernel of the one before and the copy-out of the one before that overlap.
 fx_status host_pipeline(fx_plan *p, const HostJob *jobs, int32_t n) {
+  NvtxRange range("fx host pipeline");
   DeviceScope dev(p->device);
   if (!dev.ok) return FX_ERR_CUDA;
   size_t need_in = 0, need_out = 0;
@@ -658,6 +661,7 @@ fx_status host_pipeline(fx_plan *p, const HostJob *jobs, int32_t n) {
     const int64_t small = std::max<int64_t>(64, band / 4);
     for (int64_t y0 = 0, y1 = 0; y0 < height && e == cudaSuccess; y0 = y1, ++k) {
       const int slot = k % kHostSlots;
+      NvtxRange chunk_range("fx host chunk (copy in, extract, copy out)");
       int64_t rows = band;
       if (i == 0 && y0 == 0) rows = small;
       const int64_t left = height - y0;

@@ -263,7 +263,7 @@ class TorchBackend:
     def copy_in(self, dev, image):
         t = self.torch
         src = t.from_numpy(image)
-        with t.cuda.stream(self.copy_stream):
+        with t.cuda.nvtx.range("serve: copy in"), t.cuda.stream(self.copy_stream):
             dev["img"].copy_(src, non_blocking=True)
             ev = t.cuda.Event()
             ev.record(self.copy_stream)
@@ -274,7 +274,8 @@ class TorchBackend:
     def launch(self, slot, devs):
         t = self.torch
         s = self.streams[slot]
-        self.plans[slot].extract_batch([(d["img"], d["out"]) for d in devs], stream=s)
+        with t.cuda.nvtx.range(f"serve: launch {len(devs)} requests"):
+            self.plans[slot].extract_batch([(d["img"], d["out"]) for d in devs], stream=s)
         ev = t.cuda.Event()
         ev.record(s)
         for d in devs:  # the caching allocator must not recycle these before the kernel ends

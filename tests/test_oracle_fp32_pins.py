@@ -214,3 +214,38 @@ def test_tolerance_excuses_only_near_fragile_sites():
     got[15, 3] = 1
     with pytest.raises(AssertionError):
         tolerance.check(got, exp, exc, cap=1.0)
+
+
+def test_north_star_rule_excuses_only_tiny_responses():
+    """The literal rule: a difference is excused only at a pixel whose exact
+    |L| is below 1e-5 of the range of L over its 5x5 window, in either branch;
+    the edge pixels of a step (|L| = 100 against a range of 200) are not."""
+    L1 = np.full((20, 20), 100.0)
+    L1[:, 10:] = -100.0
+    L1[5, 3] = 1e-7
+    L2 = np.full((20, 20), 7.0)
+    L2[12, 12] = 0.0                   # an exact zero inside a flat patch: range 7, excused
+    exc = tolerance.north_star_excused([L1, L2])
+    assert exc[5, 3] and exc[12, 12]
+    assert not exc[5, 9] and not exc[5, 10] and not exc[0, 0]
+    assert int(exc.sum()) == 2
+    exp = np.zeros((20, 20), np.uint8)
+    got = exp.copy()
+    got[5, 3] = 1
+    assert tolerance.check(got, exp, exc, cap=1.0) == 1
+    got[5, 9] = 1
+    with pytest.raises(AssertionError):
+        tolerance.check(got, exp, exc, cap=1.0)
+
+
+def test_north_star_rule_on_the_oracle_itself():
+    img = scenes.pan_512_u8()[:64, :96].copy()
+    p = params()
+    exp = oracle.extract(img, p)
+    assert tolerance.compare_north_star(img, exp.copy(), p) == 0
+    bad = exp.copy()
+    _, st = oracle.extract(img, p, stages=True)
+    ys, xs = np.nonzero(~tolerance.north_star_excused([st["L1"], st["L2"]]))
+    bad[ys[0], xs[0]] ^= 1
+    with pytest.raises(AssertionError):
+        tolerance.compare_north_star(img, bad, p)

@@ -141,6 +141,43 @@ def test_step_edge_closed_forms(a, b):
     assert out[:, 20 if D > 0 else 19].all()
 
 
+@pytest.mark.parametrize("D", [40, -40])
+@pytest.mark.parametrize("transpose", [False, True])
+def test_crossing_map_deviation_closed_forms(D, transpose):
+    """Standard deviation over the zero-crossing map (reading R4, source 1) on a
+    step edge.  The crossing map is one full line, so the 5x5 window of a line
+    pixel holds n = 5 crossings and its 3x3 window n = 3 (borders replicate the
+    line).  Eq. 2 over n ones and Lambda - n zeros gives
+    D = Lambda sum z^2 - (sum z)^2 = n (Lambda - n): D5 = 5 x 20 = 100 and
+    D3 = 3 x 6 = 18, so s5 = sqrt(100 / (25 x 24)) = sqrt(1/6) = 0.40825 and
+    s3 = sqrt(18 / (9 x 8)) = 1/2."""
+    img = _step(1000, 1000 + D)
+    if transpose:
+        img = np.ascontiguousarray(img.T)
+    line = 20 if D > 0 else 19
+    s5, s3 = math.sqrt(5 * 20 / (25 * 24)), math.sqrt(3 * 6 / (9 * 8))
+    assert abs(s5 - math.sqrt(1 / 6)) < 1e-15 and s3 == 0.5
+
+    def run(t5, tmax, t3):
+        p = params(stddev_source=1, t_zc=(0.0, 0.0), t_sd5=(t5, t5), t_sdmax=(tmax, tmax), t_sd3=(t3, t3), hmf=())
+        out = oracle.extract(img, p)
+        return out.T if transpose else out
+
+    full = np.zeros((30, 40), np.uint8)
+    full[:, line] = 1
+    # the 5x5 test decides while s5 <= t_sdmax
+    assert np.array_equal(run(0.408, 10.0, 10.0), full)          # 0.408^2 x 600 = 99.9 < 100
+    assert not run(0.409, 10.0, 0.0).any()                       # 0.409^2 x 600 = 100.4 > 100
+    # above t_sdmax the 3x3 window decides: s3 = 1/2
+    assert np.array_equal(run(10.0, 0.3, 0.49), full)            # 0.49^2 x 72 = 17.3 < 18
+    assert not run(0.0, 0.3, 0.51).any()                         # 0.51^2 x 72 = 18.7 > 18
+    assert not run(0.0, 0.3, 0.5).any()                          # s3 > 1/2 is strict
+    # brute force agrees on the same image
+    p = params(stddev_source=1, t_zc=(0.0, 0.0), t_sd5=(0.408, 0.408), t_sdmax=(10.0, 10.0),
+               t_sd3=(10.0, 10.0), hmf=())
+    assert np.array_equal(oracle.extract(img, p), _brute(img, p))
+
+
 @pytest.mark.parametrize("hmf", [(), (5,), (3,)])
 @pytest.mark.parametrize("a,b", [(100, 160), (160, 100)])
 def test_tiny_images_hand_cases(a, b, hmf):
