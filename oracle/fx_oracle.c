@@ -43,10 +43,11 @@
  *       The values a are the image (source 0) or the binary zero-crossing
  *       map of the same branch (source 1).
  *   R5  The two extracted maps are OR-combined.
- *   R6  Hybrid median with window k (3 or 5): the '+' subgroup is the
- *       centre row and column segment (2k-1 pixels), the 'x' subgroup the
- *       two diagonals (2k-1 pixels); output = median(med+, medx, centre).
- *       A list of windows applies the filter repeatedly, in order.
+ *   R6  Hybrid median with window k (3, 5 or 7; Sec. 3.4 leaves the size to
+ *       the application): the '+' subgroup is the centre row and column
+ *       segment (2k-1 pixels), the 'x' subgroup the two diagonals (2k-1
+ *       pixels); output = median(med+, medx, centre).  A list of windows
+ *       applies the filter repeatedly, in order (Sec. 4, Sec. 4.2).
  *   R7  Output is a uint8 image of 0/1.
  *   R9  FP32-LoG mode (log_mode 1, non-integer masks): the mean-removed
  *       samples of R1, scaled to max |w| = Q, are rounded half away from zero
@@ -288,7 +289,7 @@ static double median_of(double *v, int n) { /* insertion sort, then middle */
 /* Sec. 3.4 with reading R6: hybrid median of window k at every pixel of O. */
 static void stage_hmf(plane *M, int k, plane *O) {
   int r = k / 2;
-  double plus[9], cross[9], three[3];
+  double plus[13], cross[13], three[3]; /* 2k - 1 <= 13 */
   for (long long y = O->y_lo; y < O->y_hi; ++y)
     for (long long x = 0; x < O->W; ++x) {
       int np = 0, nc = 0;
@@ -332,7 +333,7 @@ int fxo_extract(const void *img, int elem, long long W, long long H, long long p
   for (int i = 0; i < ORACLE_MAX_HMF; ++i) {
     int k = (int)prm[P_HMF0 + i];
     if (k == 0) break;
-    if (k != 3 && k != 5) return O_BAD_ARG;
+    if (k != 3 && k != 5 && k != 7) return O_BAD_ARG;
     hmf[nh++] = k;
     r_m += k / 2;
   }
@@ -424,7 +425,7 @@ int fxo_extract(const void *img, int elem, long long W, long long H, long long p
 int fxo_hybrid_median(const void *img, int elem, long long W, long long H, long long pitch,
                       int k, uint16_t *out) {
   if (!img || !out || (elem != 1 && elem != 2) || W < 1 || H < 1 || pitch < W * elem) return O_BAD_ARG;
-  if (k != 3 && k != 5) return O_BAD_ARG;
+  if (k != 3 && k != 5 && k != 7) return O_BAD_ARG;
   image im = {(const uint8_t *)img, elem, W, H, pitch};
   plane P, O;
   if (plane_init(&P, W, H, 0, H) != O_OK) return O_NOMEM;

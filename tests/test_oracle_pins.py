@@ -311,27 +311,67 @@ def test_hmf_exhaustive_binary(k):
         assert _hmf_expect(pats[i], k) == expect[i]
 
 
-def test_hmf_grayscale_against_numpy_median():
-    rng = np.random.default_rng(5)
-    pats = rng.integers(0, 65536, size=(3000, 5, 5)).astype(np.uint16)
-    img, cols = _tile_patterns(pats, 5)
-    out = oracle.hybrid_median(img, 5)
-    got = out[2::5, 2::5].reshape(-1)[:3000]
-    assert all(int(got[i]) == _hmf_expect(pats[i], 5) for i in range(3000))
+def test_hmf7_random_binary_patterns():
+    """Window 7 (13 pixels in each subgroup, 25 distinct cells): 2^25 patterns
+    are too many to enumerate, so 120000 random ones with a random density per
+    pattern (every count of ones occurs), against the subgroup majorities, and
+    a spot check of those against numpy's median on the windows."""
+    k, r = 7, 3
+    cells = [(r, r)] + [(r, r + d) for d in range(-r, r + 1) if d] + \
+            [(r + d, r) for d in range(-r, r + 1) if d] + \
+            [(r + d, r + d) for d in range(-r, r + 1) if d] + \
+            [(r - d, r + d) for d in range(-r, r + 1) if d]
+    assert len(cells) == 25
+    rng = np.random.default_rng(77)
+    n = 120000
+    dens = rng.random(n)[:, None]
+    bits = (rng.random((n, 25)) < dens).astype(np.uint8)
+    pats = rng.integers(0, 2, size=(n, k, k)).astype(np.uint8)  # cells off the groups are noise
+    for j, (y, x) in enumerate(cells):
+        pats[:, y, x] = bits[:, j]
+    img, cols = _tile_patterns(pats, k)
+    out = oracle.hybrid_median(img, k)
+    centres = out[r::k, r::k].reshape(-1)[:n]
+    plus_idx = [0] + list(range(1, 13))
+    cross_idx = [0] + list(range(13, 25))
+    mp = (bits[:, plus_idx].sum(1) >= 7).astype(int)
+    mx = (bits[:, cross_idx].sum(1) >= 7).astype(int)
+    expect = ((mp + mx + bits[:, 0]) >= 2).astype(np.uint8)
+    assert np.array_equal(centres, expect)
+    assert len(set(bits[:, plus_idx].sum(1))) == 14  # counts 0 .. 13 all occur
+    for i in rng.integers(0, n, 300):
+        assert _hmf_expect(pats[i], k) == expect[i]
 
 
-def test_hmf_salt_pepper_and_lines():
+@pytest.mark.parametrize("k", [5, 7])
+def test_hmf_grayscale_against_numpy_median(k):
+    rng = np.random.default_rng(5 + k)
+    pats = rng.integers(0, 65536, size=(3000, k, k)).astype(np.uint16)
+    img, cols = _tile_patterns(pats, k)
+    out = oracle.hybrid_median(img, k)
+    got = out[k // 2::k, k // 2::k].reshape(-1)[:3000]
+    assert all(int(got[i]) == _hmf_expect(pats[i], k) for i in range(3000))
+
+
+@pytest.mark.parametrize("k", [3, 5, 7])
+def test_hmf_salt_pepper_and_lines(k):
     """Sec. 3.4 / Sec. 2: isolated impulses are removed, thin lines (axis and
-    45 degrees) survive."""
-    z = np.zeros((15, 15), np.uint8)
-    s = z.copy(); s[7, 7] = 1
-    assert not oracle.hybrid_median(s, 5).any()
-    p = np.ones_like(z); p[7, 7] = 0
-    assert oracle.hybrid_median(p, 5).all()
+    45 degrees) survive: on a line the '+' group holds k of its 2k - 1
+    pixels (the line's column) and the centre is set, so the median keeps
+    it; next to the line both groups hold at most one set pixel."""
+    z = np.zeros((17, 17), np.uint8)
+    s = z.copy(); s[8, 8] = 1
+    assert not oracle.hybrid_median(s, k).any()
+    p = np.ones_like(z); p[8, 8] = 0
+    assert oracle.hybrid_median(p, k).all()
     v = z.copy(); v[:, 6] = 1
-    assert np.array_equal(oracle.hybrid_median(v, 5), v)
-    d = np.eye(15, dtype=np.uint8)
-    assert np.array_equal(oracle.hybrid_median(d, 5), d)
+    assert np.array_equal(oracle.hybrid_median(v, k), v)
+    d = np.eye(17, dtype=np.uint8)
+    assert np.array_equal(oracle.hybrid_median(d, k), d)
+    # a 2 x 2 speck is removed by window 7 (each group holds at most 3 of 13)
+    q = z.copy(); q[8:10, 8:10] = 1
+    if k == 7:
+        assert not oracle.hybrid_median(q, k).any()
 
 
 # ---------------------------------------------------------------- Eq. 2
@@ -381,7 +421,7 @@ D4 = [
 ]
 
 
-@pytest.mark.parametrize("hmf", [(), (5,), (3,), (5, 3)])
+@pytest.mark.parametrize("hmf", [(), (5,), (3,), (5, 3), (7,), (7, 5, 3)])
 @pytest.mark.parametrize("source", [0, 1])
 def test_dihedral_equivariance(hmf, source):
     """The masks, the 4-neighbourhood, the windows and the '+'/'x' subgroups
@@ -469,7 +509,7 @@ def test_brute_force_all_3x3_images():
     assert fired > 1000
 
 
-@pytest.mark.parametrize("seed", range(12))
+@pytest.mark.parametrize("seed", range(18))
 def test_brute_force_random_tiny_images(seed):
     rng = np.random.default_rng(seed)
     H, W = int(rng.integers(1, 18)), int(rng.integers(1, 14))
@@ -484,7 +524,7 @@ def test_brute_force_random_tiny_images(seed):
              t_sdmax=tuple(float(rng.integers(20 * sc, 90 * sc)) for _ in range(2)),
              t_sd3=tuple(float(rng.integers(0, 50 * sc)) for _ in range(2)),
              stddev_source=int(seed % 4 == 1),
-             hmf=[(), (5,), (3,), (5, 3)][seed % 4])
+             hmf=[(), (5,), (3,), (5, 3), (7,), (7, 5, 3)][seed % 6])
     if p["stddev_source"]:
         p.update(t_sd5=(0.2, 0.3), t_sdmax=(0.45, 0.5), t_sd3=(0.3, 0.4))
     assert np.array_equal(oracle.extract(img, p), _brute(img, p))
