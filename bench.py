@@ -148,7 +148,7 @@ class ClockSampler:
 
 # ------------------------------------------------------------- profiles
 
-KERNEL_SOURCES = ("fx_internal.h", "fx_stream.cuh", "fx_stream.cu")
+KERNEL_SOURCES = ("fx_internal.h", "fx_stream.cuh", "fx_stream_kernels.cuh", "fx_stream.cu")
 
 
 def kernel_source_sha() -> str:
@@ -443,7 +443,10 @@ def bench_variants(fx, torch, stream, band, out, band_np, reps=5):
         "median_off": (dict(hmf=()), "streaming"),
         "median_3": (dict(hmf=(3,)), "streaming"),
         "median_5_then_3": (dict(hmf=(5, 3)), "streaming"),
-        "median_5_then_5": (dict(hmf=(5, 5)), "general tile"),
+        "median_7": (dict(hmf=(7,)), "streaming"),
+        "median_5_then_5": (dict(hmf=(5, 5)), "streaming, wide strips"),
+        "median_7_5_3": (dict(hmf=(7, 5, 3)), "streaming, wide strips"),
+        "median_7_7_7": (dict(hmf=(7, 7, 7)), "general tile"),
         "stddev_over_crossing_map": (dict(stddev_source=1, t_sd5=(0.2, 0.3), t_sdmax=(0.45, 0.5),
                                           t_sd3=(0.3, 0.4)), "streaming"),
     }

@@ -88,8 +88,11 @@ typedef struct {
   /* 0 = the standard deviation is taken over the image (default); 1 = over
    * the binary zero-crossing map of the same branch (Sec. 4.1 literal). */
   int32_t stddev_source;
-  /* Hybrid-median windows applied in order (3 or 5; 0 ends the list).
-   * Default {5, 0, 0, 0}; all zero switches the filter off. */
+  /* Hybrid-median windows applied in order (3, 5 or 7; 0 ends the list;
+   * Sec. 3.4 leaves the size to the application, Sec. 4.2 repeats the filter
+   * with several sizes).  Default {5, 0, 0, 0}; all zero switches the filter
+   * off.  fx_extract runs lists whose radii (window / 2) add up to at most 7
+   * in its fused streaming kernel, longer ones in the general tile kernel. */
   int32_t hmf[FX_MAX_HMF_LEVELS];
   /* Nominal radiometric depth used only to scale the default thresholds
    * (value scale 2^(bits-8)); it never restricts the input values. */
@@ -215,7 +218,7 @@ fx_status fx_extract_batch(fx_plan *plan, const fx_image_desc *descs, int32_t n,
  * fastest; fx_plan_set_tile forces one.  In both calls tile_h 0 stands for the
  * automatic height (picked per batch for the given CTAs per SM).  Plans whose
  * parameters need the general kernel (median windows whose radii add up to
- * more than 3, or more than two levels) use its fixed 64 x 32 tile; for them
+ * more than 3) use its fixed 64 x 32 tile; for them
  * only ctas_per_sm takes effect.
  * Errors: FX_ERR_INVALID_ARG (shape or count out of range), FX_ERR_CUDA.
  */

@@ -80,7 +80,7 @@ fx_status make_kparams(const fx_params *p, int32_t maxval, KParams *kp) {
   for (int i = 0; i < FX_MAX_HMF_LEVELS; ++i) {
     int k = p->hmf[i];
     if (k == 0) break;
-    if (k != 3 && k != 5) return FX_ERR_INVALID_ARG;
+    if (k != 3 && k != 5 && k != 7) return FX_ERR_INVALID_ARG;
     kp->hmf[kp->nhmf++] = k;
     kp->r_m += k / 2;
   }

@@ -90,7 +90,10 @@ struct ImageView {
 };
 
 cudaError_t launch_tile_general(const ImageView &v, const KParams &kp, cudaStream_t s);
-bool fast_path_supported(const KParams &kp);
+bool fast_path_supported(const KParams &kp);  // the streaming kernels (narrow or wide strips)
+bool stream_narrow(const KParams &kp);        // the narrow strips (also the batched kernels)
+cudaError_t launch_wide(const ImageView &v, const KParams &kp, cudaStream_t s, int64_t blocks, int64_t units_x,
+                        int64_t units, int uh);
 bool pair_loads_ok(const ImageView &v);
 cudaError_t launch_fast(const ImageView &v, const KParams &kp, cudaStream_t s);
 cudaError_t launch_extract(const ImageView &v, const KParams &kp, cudaStream_t s);

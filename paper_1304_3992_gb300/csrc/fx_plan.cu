@@ -440,7 +440,7 @@ fx_status fx_plan_create(fx_plan **out, const fx_params *params, int32_t max_ima
   }
   p->st16 = make_kparams(params, 65535, &p->kp16);
   if (p->st16 != FX_OK) p->kp16 = p->kp8;
-  p->fast = fast_path_supported(p->kp8) && fast_path_supported(p->kp16);
+  p->fast = stream_narrow(p->kp8) && stream_narrow(p->kp16);
   p->device = device;
   p->max_images = max_images;
   p->unit_w = strip_width(p->kp8.source == 1);

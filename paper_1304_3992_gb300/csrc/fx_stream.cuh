@@ -49,8 +49,12 @@
 namespace fx {
 
 // Output columns of a strip: 52, or 48 when the standard deviation is taken
-// over the crossing map (its 5x5 window adds 2 columns to the halo).
-constexpr int strip_width(bool src_z) { return src_z ? 48 : 52; }
+// over the crossing map (its 5x5 window adds 2 columns to the halo); wide
+// strips (median lists whose radii add up to 4 .. 7) have 4 more halo columns
+// on each side: 44, or 40.
+constexpr int strip_width(bool src_z, bool wide = false) { return (wide ? 44 : 52) - (src_z ? 4 : 0); }
+// Largest sum of median radii of the narrow and the wide strips.
+constexpr int kNarrowRm = 3, kWideRm = 7;
 constexpr int kDefaultUnitH = 512;
 // unit heights the batched plan's autotuner times
 constexpr int kNumUnitHeights = 4;
@@ -87,6 +91,8 @@ __device__ __forceinline__ uint32_t n1(uint32_t o, uint32_t pb) { return __funne
 __device__ __forceinline__ uint32_t s1(uint32_t o, uint32_t nb) { return __funnelshift_l(nb, o, 2); }
 __device__ __forceinline__ uint32_t n2(uint32_t o, uint32_t pb) { return __funnelshift_r(o, pb, 4); }
 __device__ __forceinline__ uint32_t s2(uint32_t o, uint32_t nb) { return __funnelshift_l(nb, o, 4); }
+__device__ __forceinline__ uint32_t n3(uint32_t o, uint32_t pb) { return __funnelshift_r(o, pb, 6); }
+__device__ __forceinline__ uint32_t s3(uint32_t o, uint32_t nb) { return __funnelshift_l(nb, o, 6); }
 
 __device__ __forceinline__ void fadd(uint32_t a, uint32_t b, uint32_t c, uint32_t &s, uint32_t &k) {
   s = a ^ b ^ c;
@@ -112,6 +118,19 @@ __device__ __forceinline__ uint32_t maj9(const uint32_t x[9]) {
   const uint32_t at2 = (c1 & c2) | (c3 & c4) | ((c1 | c2) & (c3 | c4));
   const uint32_t at3 = (c1 & c2 & (c3 | c4)) | (c3 & c4 & (c1 | c2));
   return at3 | (at2 & s4);
+}
+// bitwise "at least 7 of 13": weight-1 bits s1..s4 and x[12] counted to
+// p0 + 2 p1 + 4 p2, weight-2 carries c1..c4 and p1 to q0 + 2 q1 + 4 q2 (in units
+// of 2), so the total is p0 + 2 q0 + 4 (q1 + p2) + 8 q2
+__device__ __forceinline__ uint32_t maj13(const uint32_t x[13]) {
+  uint32_t s1, c1, s2, c2, s3, c3, s4, c4, p0, p1, p2, q0, q1, q2;
+  fadd(x[0], x[1], x[2], s1, c1);
+  fadd(x[3], x[4], x[5], s2, c2);
+  fadd(x[6], x[7], x[8], s3, c3);
+  fadd(x[9], x[10], x[11], s4, c4);
+  count5(s1, s2, s3, s4, x[12], p0, p1, p2);
+  count5(c1, c2, c3, c4, p1, q0, q1, q2);
+  return q2 | (q1 & p2) | ((q1 ^ p2) & q0 & p0);
 }
 // bitwise "at least 3 of 5"
 __device__ __forceinline__ uint32_t maj5(const uint32_t x[5]) {
@@ -288,12 +307,18 @@ struct Ar<kModeF32LogWide> : Ar<kModeF32> {
 // kSd2: the branches have different standard-deviation thresholds (two S words).
 // kSrcZ: the standard deviation is taken over each branch's crossing map
 // (reading R4, source 1) from bit-sliced counts, at block level.
-template <typename T, int kMode, bool kPair, bool kSd2, bool kSrcZ>
+// kWide: median lists whose radii add up to 4 .. 7 (a wider halo, and the
+// ring prefill one iteration earlier, so that the rows above the unit that the
+// outputs depend on are computed).
+template <typename T, int kMode, bool kPair, bool kSd2, bool kSrcZ, bool kWide = false>
 struct Strip {
   using A = Ar<kMode>;
   // halo columns left of the strip (even: the pair loads are aligned) and
-  // output columns: 2 LoG + 1 crossing (+ 2 standard deviation) + up to 3 median
-  static constexpr int kLeftHalo = kSrcZ ? 8 : 6, kOutCols = strip_width(kSrcZ);
+  // output columns: 2 LoG + 1 crossing (+ 2 standard deviation) + up to 3 (7)
+  // median
+  static constexpr int kLeftHalo = (kWide ? 10 : 6) + (kSrcZ ? 2 : 0), kOutCols = strip_width(kSrcZ, kWide);
+  static_assert(2 * kLeftHalo + kOutCols == 64, "symmetric halo");
+  static constexpr int kK0 = kWide ? -3 : -2;  // first iteration (rows 4 kK0 .. are the ring prefill)
   using V = typename A::V;
   using P = typename A::P;
   using Q = typename A::Q;
@@ -320,13 +345,13 @@ struct Strip {
   uint32_t acc_[12];
   // Words of earlier blocks, touched once per 16 rows, live in shared memory:
   // kBlk.. = previous block (12 words), kPneg / kPpos / kPsS = neg / pos / sS of
-  // the block before it, kMA / kMB = mask words of the two previous blocks,
-  // kHA / kHB = first median level's words of the two blocks before (two levels),
-  // kZA / kZB = crossing words of the two blocks before and kPcf = contrast words
-  // of the block before (kSrcZ).
+  // the block before it, kLev + 2l / + 2l + 1 = the words of median level l
+  // (level 0: the mask M) of the two blocks before, kZA / kZB = crossing words
+  // of the two blocks before and kPcf = contrast words of the block before
+  // (kSrcZ).
   uint32_t (*sw_)[32];
-  static constexpr int kBlk = 0, kPneg = 12, kPpos = 14, kPsS = 16, kMA = 18, kMB = 19, kHA = 20, kHB = 21,
-                       kZA = 22, kZB = 24, kPcf = 26, kWords = 28;
+  static constexpr int kBlk = 0, kPneg = 12, kPpos = 14, kPsS = 16, kLev = 18, kMA = kLev, kZA = 26, kZB = 28,
+                       kPcf = 30, kWords = 32;
   // kAsync (uint16 pixel pairs on the FP32 paths): the input rows arrive in an
   // 8-row ring of words in shared memory (kRing .. kRing + 7), filled by
   // cp.async seven rows ahead, so loads in flight hold no registers.
@@ -372,8 +397,10 @@ struct Strip {
     rhi = static_cast<int32_t>(hi - Y0);
     Hrel = static_cast<int32_t>(H - Y0);
     Y0rel = static_cast<int32_t>(Y0 < (1 << 30) ? Y0 : (1 << 30));
-    // rows a unit reads are >= Y0 - 8; offsets from there fit 32 bits times the pitch
-    rbase = rlo > -8 ? rlo : -8;
+    // rows a unit reads are >= Y0 + 4 kK0 (the first prefill row) and >= the
+    // buffer's first row; load offsets count from there, so they are never
+    // negative
+    rbase = rlo > 4 * kK0 ? rlo : 4 * kK0;
     pitch32 = static_cast<uint32_t>(v.pitch);
     const unsigned char *base = static_cast<const unsigned char *>(v.img) + (Y0 + rbase - v.row0) * v.pitch;
     const int64_t d0 = x < 0 ? 0 : (x >= W ? W - 1 : x), d1 = x + 1 < 0 ? 0 : (x + 1 >= W ? W - 1 : x + 1);
@@ -801,6 +828,17 @@ struct Strip {
                                  n2(oX, pX), n2(oP, pP), s2(oX, xX), s2(oP, xP)};
       return maj3(maj9(plus), maj9(cross), own);
     }
+    if (k == 7) {  // three columns over: the neighbour lane's one-column shifts
+      const uint32_t E3o = __shfl_down_sync(kFull, E1o, 1), W3o = __shfl_up_sync(kFull, W1o, 1);
+      const uint32_t E3p = __shfl_down_sync(kFull, E1p, 1), W3p = __shfl_up_sync(kFull, W1p, 1);
+      const uint32_t E3n = __shfl_down_sync(kFull, E1n, 1), W3n = __shfl_up_sync(kFull, W1n, 1);
+      const uint32_t plus[13] = {own, E1o, W1o, oX, oP, E3o, W3o, n1(own, prev), s1(own, next),
+                                 n2(own, prev), s2(own, next), n3(own, prev), s3(own, next)};
+      const uint32_t cross[13] = {own, n1(E1o, E1p), n1(W1o, W1p), s1(E1o, E1n), s1(W1o, W1n),
+                                  n2(oX, pX), n2(oP, pP), s2(oX, xX), s2(oP, xP),
+                                  n3(E3o, E3p), n3(W3o, W3p), s3(E3o, E3n), s3(W3o, W3n)};
+      return maj3(maj13(plus), maj13(cross), own);
+    }
     const uint32_t plus[5] = {own, E1o, W1o, n1(own, prev), s1(own, next)};
     const uint32_t cross[5] = {own, n1(E1o, E1p), n1(W1o, W1p), s1(E1o, E1n), s1(W1o, W1n)};
     return maj3(maj5(plus), maj5(cross), own);
@@ -858,7 +896,7 @@ struct Strip {
 #pragma unroll
       for (int f = 0; f < 2; ++f)
         if (g >= 0) z[f] = replicate(g - 1, crossings(f), sw_[kZA + f][lane]);
-      if (g >= 2) {
+      if (g >= 1) {  // from block -1 on: wide median lists reach the rows above the unit
 #pragma unroll
         for (int f = 0; f < 2; ++f) {
           const uint32_t za = sw_[kZA + f][lane];
@@ -874,19 +912,28 @@ struct Strip {
       }
     } else {
       gm = g - 1;
-      if (g >= 1) m = mask_block(g - 1);
+      if (g >= 0) m = mask_block(g - 1);  // from block -1 on: wide median lists reach the rows above the unit
     }
-    if (kp.nhmf < 2) {
-      if (gm >= 1) store(gm - 1, kp.nhmf ? median(sw_[kMB][lane], sw_[kMA][lane], m, kp.hmf[0]) : sw_[kMA][lane]);
-    } else {  // two median levels: the first one's words are a stage of their own
-      uint32_t h1 = 0;
-      if (gm >= 1) h1 = replicate(gm - 1, median(sw_[kMB][lane], sw_[kMA][lane], m, kp.hmf[0]), sw_[kHA][lane]);
-      if (gm >= 2) store(gm - 2, median(sw_[kHB][lane], sw_[kHA][lane], h1, kp.hmf[1]));
-      sw_[kHB][lane] = sw_[kHA][lane];
-      sw_[kHA][lane] = h1;
+    // Median levels (Sec. 3.4, repeated per Sec. 4.2): level l + 1 of block
+    // gm - l - 1 from level l of blocks gm - l - 2 .. gm - l; every level but
+    // the last is a replicated stage (reading R2).  Without a median the mask
+    // of block gm - 1 is stored (the same one block of delay).
+    const int nl = kp.nhmf;
+    uint32_t cur = m;
+    if (nl == 0) {
+      cur = sw_[kLev][lane];
+      sw_[kLev][lane] = m;
     }
-    sw_[kMB][lane] = sw_[kMA][lane];
-    sw_[kMA][lane] = m;
+#pragma unroll 1
+    for (int l = 0; l < nl; ++l) {
+      const uint32_t a = sw_[kLev + 2 * l][lane], b = sw_[kLev + 2 * l + 1][lane];
+      sw_[kLev + 2 * l + 1][lane] = a;
+      sw_[kLev + 2 * l][lane] = cur;
+      const uint32_t h = median(b, a, cur, kp.hmf[l]);
+      cur = l + 1 < nl ? replicate(gm - l - 1, h, sw_[kLev + 2 * l + 2][lane]) : h;
+    }
+    const int64_t gs = gm - (nl > 1 ? nl : 1);  // block of the stored words
+    if (gs >= 0) store(gs, cur);
 #pragma unroll
     for (int f = 0; f < 2; ++f) {
       sw_[kPneg + f][lane] = blk(5 * f);
@@ -910,30 +957,31 @@ struct Strip {
   // launches; the batched kernels, whose units are long, run without it).
   template <bool kTail = true>
   __device__ bool run() {
-    // Rows Y0-8 .. Y0-1 (k = -2, -1) fill the rings; they compute responses and
-    // bits of rows no output depends on.  Bit blocks span 16 rows (four
+    // Rows Y0-8 .. Y0-1 (k = -2, -1; from Y0-12 for wide strips) fill the rings;
+    // they compute the rows above the unit that its outputs depend on (the mask
+    // rows down to Y0 - r_m).  Bit blocks span 16 rows (four
     // iterations); block b covers rows [Y0 - 3 + 16b, Y0 + 13 + 16b) and its
     // median is stored at the end of group b + 2.
     if constexpr (kAsync) {
-      // rows -8 .. -2 into slots 0 .. 6 (slot of row t = t & 7); each step
-      // refills the slot read one step before with the row seven ahead
+      // rows 4 kK0 .. 4 kK0 + 6 into their slots (slot of row t = t & 7); each
+      // step refills the slot read one step before with the row seven ahead
 #pragma unroll
-      for (int i = 0; i < kRingRows - 1; ++i) load_row_async(ring_h_ + 128u * i, i - 8);
+      for (int i = 0; i < kRingRows - 1; ++i) load_row_async(ring_h_ + 128u * ((4 * kK0 + i) & 7), 4 * kK0 + i);
     } else {
-      load_row<0>(-8);
-      load_row<1>(-7);
-      load_row<2>(-6);
-      load_row<3>(-5);
+      load_row<0>(4 * kK0);
+      load_row<1>(4 * kK0 + 1);
+      load_row<2>(4 * kK0 + 2);
+      load_row<3>(4 * kK0 + 3);
     }
     const uint32_t ring0 = ring_h_;
     const int32_t bmax = static_cast<int32_t>((Y1 - Y0 + 2) / 16);
     // one more block of delay per extra median level and for the crossing-map source
-    const int32_t iters = 4 * (bmax + (kp.nhmf < 2 ? 3 : 4) + (kSrcZ ? 1 : 0));
+    const int32_t iters = 4 * (bmax + 2 + (kp.nhmf > 1 ? kp.nhmf : 1) + (kSrcZ ? 1 : 0));
     // the last step whose row feeds an output: the bits of row r are packed at
     // step r + 3, and the last output row needs the median radius, its south
     // neighbour (+1) and, for the crossing-map source, the deviation's 2 rows
     [[maybe_unused]] const int32_t t_end = static_cast<int32_t>(Y1 - Y0 - 1) + kp.r_m + 4 + (kSrcZ ? 2 : 0);
-    for (int32_t k = -2; k < iters; ++k) {
+    for (int32_t k = kK0; k < iters; ++k) {
       if constexpr (kTail) {
         if (4 * k > t_end) {
           // past the rows any output needs: keep the bit positions of the block
@@ -992,42 +1040,42 @@ __device__ __forceinline__ uint8_t *unit_marker(const ImageView &v, int64_t ux, 
 
 // Per-warp shared words of the streaming path (the caller's kernel owns one
 // array of this type per CTA and passes the warp's slice).
-constexpr int kStripWords = 36;  // 28 block words + the 8-row input ring
+constexpr int kStripWords = 40;  // 32 block words + the 8-row input ring
 using StripWords = uint32_t[kWarpsPerCta][kStripWords][32];
 __device__ __forceinline__ uint32_t (*warp_words(StripWords &w))[32] { return w[(threadIdx.x >> 5) % kWarpsPerCta]; }
 
 // kF32Log selects the FP32-LoG mode (KParams::f32log) at compile time; kSd2 =
 // !KParams::sd_same (kSd2 = true is correct for any thresholds); kSrcZ =
-// (KParams::source == 1).
-template <typename T, bool kF32Log, bool kPair, bool kSd2, bool kSrcZ, bool kTail = true>
+// (KParams::source == 1); kWide = median radii adding up to more than 3.
+template <typename T, bool kF32Log, bool kPair, bool kSd2, bool kSrcZ, bool kTail = true, bool kWide = false>
 __device__ __forceinline__ void fast_unit(const ImageView &v, const KParams &kp, int64_t ux, int64_t uy, int,
                                           int uh, uint32_t (*words)[32]) {
   constexpr int kMode = kF32Log ? st::kModeF32Log : st::kModeF32;
-  static_assert(st::Strip<T, kMode, kPair, kSd2, kSrcZ>::kWords + st::Strip<T, kMode, kPair, kSd2, kSrcZ>::kRingRows ==
-                    kStripWords,
-                "shared word layout");
+  using S = st::Strip<T, kMode, kPair, kSd2, kSrcZ, kWide>;
+  static_assert(S::kWords + S::kRingRows == kStripWords, "shared word layout");
   if (kp.fbound < 0) return;
-  constexpr int uw = strip_width(kSrcZ);
+  constexpr int uw = strip_width(kSrcZ, kWide);
   const int64_t X0 = ux * uw;
   const int64_t Y0 = v.y_begin + uy * uh;
   const int64_t Y1 = Y0 + uh < v.y_end ? Y0 + uh : v.y_end;
-  st::Strip<T, kMode, kPair, kSd2, kSrcZ> s(v, kp, X0, Y0, Y1, words);
+  S s(v, kp, X0, Y0, Y1, words);
   if (!s.template run<kTail>() && (threadIdx.x & 31) == 0) *unit_marker(v, ux, uy, uh, uw) = kRedo;
 }
 
-template <typename T, bool kF32Log, bool kSrcZ>
+template <typename T, bool kF32Log, bool kSrcZ, bool kWide = false>
 __device__ __forceinline__ void fast_unit_redo(const ImageView &v, const KParams &kp, int64_t ux, int64_t uy,
                                                int, int uh, uint32_t (*words)[32]) {
   constexpr int kMode = kF32Log ? st::kModeF32LogWide : st::kModeInt;
+  constexpr int uw = strip_width(kSrcZ, kWide);
   if (kp.fbound >= 0) {
     uint8_t mark = 0;
-    if ((threadIdx.x & 31) == 0) mark = *unit_marker(v, ux, uy, uh, strip_width(kSrcZ));
+    if ((threadIdx.x & 31) == 0) mark = *unit_marker(v, ux, uy, uh, uw);
     if (__shfl_sync(st::kFull, mark, 0) != kRedo) return;
   }
-  const int64_t X0 = ux * strip_width(kSrcZ);
+  const int64_t X0 = ux * uw;
   const int64_t Y0 = v.y_begin + uy * uh;
   const int64_t Y1 = Y0 + uh < v.y_end ? Y0 + uh : v.y_end;
-  st::Strip<T, kMode, false, true, kSrcZ> s(v, kp, X0, Y0, Y1, words);
+  st::Strip<T, kMode, false, true, kSrcZ, kWide> s(v, kp, X0, Y0, Y1, words);
   s.run();
 }
 

@@ -1,0 +1,13 @@
+// fx_stream_wide.cu -- the wide streaming strips (median lists whose radii
+// add up to 4 .. 7), compiled apart from the narrow ones.
+#include "fx_stream_kernels.cuh"
+
+namespace fx {
+
+cudaError_t launch_wide(const ImageView &v, const KParams &kp, cudaStream_t s, int64_t blocks, int64_t units_x,
+                        int64_t units, int uh) {
+  return v.elem == 1 ? launch_t<uint8_t, true>(v, kp, s, blocks, units_x, units, uh)
+                     : launch_t<uint16_t, true>(v, kp, s, blocks, units_x, units, uh);
+}
+
+}  // namespace fx

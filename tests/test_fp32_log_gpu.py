@@ -77,17 +77,19 @@ def test_fp32_ragged_sizes(cuda_lib, shape, bits):
     assert tolerance.compare_with_oracle(img, got, d) == 0
 
 
-@pytest.mark.parametrize("case", range(8))
+@pytest.mark.parametrize("case", range(11))
 def test_fp32_parameter_variants(cuda_lib, case):
-    """Median off / 3 / 5 then 3 and the crossing-map source (streaming
-    kernel), median 5 then 5 and three levels (general tile kernel), other
-    sigmas and mask scales."""
+    """Median off / 3 / 5 then 3 / 7 and the crossing-map source (narrow
+    streaming strips), median 5 then 5, 7 then 5 then 3 and three levels with
+    the crossing-map source (wide strips), 7 then 7 then 7 (general tile
+    kernel), other sigmas and mask scales."""
     img = scenes.scene(180, 140, seed=50 + case, n_rects=40, noise_sigma=16.0, impulse_frac=0.005, bits=12)
     kw = [dict(hmf=()), dict(hmf=(3,)), dict(hmf=(5, 3)),
           dict(stddev_source=1, t_sd5=(0.2, 0.3), t_sdmax=(0.45, 0.5), t_sd3=(0.3, 0.4)),
           dict(sigma=(1.0, 2.5), t_zc=(9000.0, 20000.0)), dict(mask_q=1000, t_zc=(130000.0, 500000.0)),
           dict(hmf=(5, 5)), dict(hmf=(5, 3, 3), stddev_source=1, t_sd5=(0.2, 0.3), t_sdmax=(0.45, 0.5),
-                                 t_sd3=(0.3, 0.4))][case]
+                                 t_sd3=(0.3, 0.4)),
+          dict(hmf=(7,)), dict(hmf=(7, 5, 3)), dict(hmf=(7, 7, 7))][case]
     d, p = pair(16.0, **kw)
     got = run(cuda_lib, img, p)
     assert tolerance.compare_with_oracle(img, got, d) == 0

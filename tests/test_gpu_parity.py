@@ -388,12 +388,14 @@ def test_device_pointer_checks(cuda_lib):
     assert lib.fx_extract(img.data_ptr(), 8, 8, 16, fx.FX_U16, ctypes.byref(nanp), out.data_ptr(), None) == 1
 
 
-@pytest.mark.parametrize("hmf", [(5, 3), (3, 5), (3, 3)])
-def test_two_level_median_streaming(cuda_lib, hmf):
-    """Two median levels with radii adding up to 3 run on the streaming kernel
-    (Sec. 4.2's repeated passes); full masks of images taller than one work
-    unit, both dtypes, against the oracle, and the batched plan against
-    single calls."""
+@pytest.mark.parametrize("hmf", [(5, 3), (3, 5), (3, 3), (7,), (3, 3, 3), (5, 5), (7, 5, 3), (7, 7),
+                                 (5, 3, 3, 3), (3, 3, 3, 3), (7, 7, 7)])
+def test_median_lists_streaming(cuda_lib, hmf):
+    """Median lists (Sec. 3.4 windows 3, 5, 7; Sec. 4.2's repeated passes):
+    radii adding up to 3 run on the narrow streaming strips, 4 to 7 on the wide
+    ones (7, 7, 7 on the general tile kernel); full masks of images taller than
+    one work unit, both dtypes, against the oracle, and the batched plan (narrow
+    strips or the general kernel) against single calls."""
     imgs = [scenes.scene(700, 1100, seed=61, n_rects=300, noise_sigma=24.0, impulse_frac=0.01, bits=12),
             scenes.scene(1030, 613, seed=62, n_rects=250, noise_sigma=4.0, impulse_frac=0.01, bits=8)]
     d, p = pair(16.0, hmf=hmf)
@@ -412,7 +414,7 @@ def test_two_level_median_streaming(cuda_lib, hmf):
         assert_same(pairs[0][1].cpu().numpy(), ref, f"batched hmf {hmf}")
 
 
-@pytest.mark.parametrize("hmf", [(5,), (5, 3), (3,), ()])
+@pytest.mark.parametrize("hmf", [(5,), (5, 3), (3,), (), (7,), (5, 5), (7, 5, 3)])
 def test_crossing_map_source_streaming(cuda_lib, hmf):
     """Standard deviation over the crossing map (reading R4, source 1) on the
     streaming kernel (48-column strips, bit-sliced window counts): full masks of
@@ -476,7 +478,7 @@ def test_extract_host_chunk_schedule(cuda_lib):
         assert_same(pageable_out, ref, "pageable")
 
 
-@pytest.mark.parametrize("hmf", [(), (5,), (3,)])
+@pytest.mark.parametrize("hmf", [(), (5,), (3,), (7,), (7, 5, 3)])
 def test_tiny_images_hand_cases_gpu(cuda_lib, hmf):
     """The hand-derived tiny cases of the oracle pins through the library: a
     one-row step, its one-column transpose and the 2 x 2 steps give the
@@ -490,3 +492,29 @@ def test_tiny_images_hand_cases_gpu(cuda_lib, hmf):
             got = run(cuda_lib, img, p)
             assert_same(got, oracle.extract(img, d), f"{img.shape} {a}|{b} hmf={hmf}")
         assert run(cuda_lib, row, p).nonzero()[1].tolist() == [20 if b > a else 19]
+
+
+@pytest.mark.parametrize("hmf", [(7,), (5, 5), (7, 5, 3)])
+@pytest.mark.parametrize("shape", [(1, 1), (2, 45), (45, 2), (31, 44), (97, 89), (203, 157), (77, 133)])
+def test_ragged_sizes_window7_and_wide(cuda_lib, shape, hmf):
+    """Window 7 and wide median lists on ragged sizes (widths around the 44- and
+    52-column strips, single rows and columns) against the oracle."""
+    h, w = shape
+    img = scenes.scene(w, h, seed=h * 7 + w, n_rects=max(1, h * w // 300), noise_sigma=24.0,
+                       impulse_frac=0.01, bits=12)
+    d, p = pair(16.0, hmf=hmf)
+    assert_same(run(cuda_lib, img, p), oracle.extract(img, d), f"{shape} hmf {hmf}")
+
+
+def test_wide_strips_full_range_16bit(cuda_lib):
+    """Values above the FP32-exact bound on the wide strips: the integer pass
+    recomputes the marked strips (median 7, 5, 3)."""
+    rng = np.random.default_rng(17)
+    img = scenes.scene(333, 801, seed=23, n_rects=400, noise_sigma=64.0, impulse_frac=0.01, bits=16)
+    img[200:400] = np.minimum(img[200:400].astype(np.int64) + 30000, 65535).astype(np.uint16)
+    img[500:520, 100:140] = rng.integers(50000, 65536, size=(20, 40))
+    d, p = pair(4.0, hmf=(7, 5, 3))
+    ref = oracle.extract(img, d)
+    assert ref.sum() > 0
+    assert_same(run(cuda_lib, img, p), ref, "full range, hmf 7 5 3")
+
