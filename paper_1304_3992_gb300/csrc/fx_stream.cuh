@@ -920,20 +920,22 @@ struct Strip {
     // of block gm - 1 is stored (the same one block of delay).
     const int nl = kp.nhmf;
     uint32_t cur = m;
-    if (nl == 0) {
-      cur = sw_[kLev][lane];
+    if (nl <= 1) {  // the default single level (or none) without the level loop
+      const uint32_t a = sw_[kLev][lane];
+      if (gm >= 1) store(gm - 1, nl ? median(sw_[kLev + 1][lane], a, m, kp.hmf[0]) : a);
+      sw_[kLev + 1][lane] = a;
       sw_[kLev][lane] = m;
-    }
+    } else {
 #pragma unroll 1
-    for (int l = 0; l < nl; ++l) {
-      const uint32_t a = sw_[kLev + 2 * l][lane], b = sw_[kLev + 2 * l + 1][lane];
-      sw_[kLev + 2 * l + 1][lane] = a;
-      sw_[kLev + 2 * l][lane] = cur;
-      const uint32_t h = median(b, a, cur, kp.hmf[l]);
-      cur = l + 1 < nl ? replicate(gm - l - 1, h, sw_[kLev + 2 * l + 2][lane]) : h;
+      for (int l = 0; l < nl; ++l) {
+        const uint32_t a = sw_[kLev + 2 * l][lane], b = sw_[kLev + 2 * l + 1][lane];
+        sw_[kLev + 2 * l + 1][lane] = a;
+        sw_[kLev + 2 * l][lane] = cur;
+        const uint32_t h = median(b, a, cur, kp.hmf[l]);
+        cur = l + 1 < nl ? replicate(gm - l - 1, h, sw_[kLev + 2 * l + 2][lane]) : h;
+      }
+      if (gm - nl >= 0) store(gm - nl, cur);  // the last level's words of block gm - nl
     }
-    const int64_t gs = gm - (nl > 1 ? nl : 1);  // block of the stored words
-    if (gs >= 0) store(gs, cur);
 #pragma unroll
     for (int f = 0; f < 2; ++f) {
       sw_[kPneg + f][lane] = blk(5 * f);
