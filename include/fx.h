@@ -301,6 +301,17 @@ fx_status fx_hybrid_median(const void *img, int64_t width, int64_t height, int64
 fx_status fx_extract_batch_noalloc(const fx_params *params, const fx_image_desc *descs, int32_t n,
                                    void *stream);
 
+/*
+ * Range-check failures counted by the kernels of the checked build
+ * (libfx_checked.so, compiled with FX_CHECKED: every global and shared-memory
+ * index of the kernels is checked before use; a failed check is counted and
+ * its access skipped, nothing traps).  A debugging aid of this library; the
+ * paper has no counterpart.  Synchronises the current device; *count receives
+ * the failures counted on it since the last reset, reset != 0 clears them.
+ * The normal build returns FX_ERR_UNSUPPORTED with *count = 0.
+ */
+fx_status fx_checked_violations(uint64_t *count, int32_t reset);
+
 /* Human-readable name of a status code (static storage). */
 const char *fx_status_string(fx_status s);
 

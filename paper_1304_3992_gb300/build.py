@@ -3,7 +3,7 @@
 Translation units compile in parallel (nvcc for .cu, g++ for .cpp) and link
 with nvcc into paper_1304_3992_gb300/_build/libfx.so with the CUDA runtime
 linked statically.  Rebuilds only when a source or header is newer than the
-library.  Usage: python -m paper_1304_3992_gb300.build [--force]
+library.  Usage: python -m paper_1304_3992_gb300.build [--force] [--checked]
 """
 from __future__ import annotations
 
@@ -19,6 +19,9 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libfx.so")
+# the checked build: -DFX_CHECKED range-checks every kernel memory index
+BUILD_CHECKED = os.path.join(HERE, "_build_checked")
+LIB_CHECKED = os.path.join(BUILD_CHECKED, "libfx_checked.so")
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 
@@ -38,15 +41,15 @@ def _deps():
         [os.path.join(ROOT, "include", "fx.h"), os.path.abspath(__file__)]
 
 
-def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+def up_to_date(lib: str = LIB) -> bool:
+    if not os.path.exists(lib):
         return False
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return all(os.path.getmtime(d) <= t for d in _deps())
 
 
-def _compile(src: str, extra: list[str]) -> str:
-    obj = os.path.join(BUILD, os.path.basename(src) + ".o")
+def _compile(src: str, extra: list[str], build_dir: str = BUILD) -> str:
+    obj = os.path.join(build_dir, os.path.basename(src) + ".o")
     inc = ["-I" + os.path.join(ROOT, "include"), "-I" + CSRC]
     if src.endswith(".cu"):
         extra = extra + [f"-D{k}={os.environ[k]}" for k in ("FX_FIRST_PASS_CTAS", "FX_WARPS_PER_CTA") if os.environ.get(k)]
@@ -62,25 +65,27 @@ def _compile(src: str, extra: list[str]) -> str:
     return obj
 
 
-def build(force: bool = False, verbose: bool = False, extra: list[str] | None = None) -> str:
-    """Compile every translation unit for sm_103a and link libfx.so; returns its path."""
-    if not force and up_to_date():
-        return LIB
-    os.makedirs(BUILD, exist_ok=True)
-    extra = list(extra or [])
+def build(force: bool = False, verbose: bool = False, extra: list[str] | None = None, checked: bool = False) -> str:
+    """Compile every translation unit for sm_103a and link libfx.so (or, with
+    checked=True, libfx_checked.so with -DFX_CHECKED); returns its path."""
+    build_dir, lib = (BUILD_CHECKED, LIB_CHECKED) if checked else (BUILD, LIB)
+    if not force and up_to_date(lib):
+        return lib
+    os.makedirs(build_dir, exist_ok=True)
+    extra = list(extra or []) + (["-DFX_CHECKED"] if checked else [])
     srcs = _sources()
     with cf.ThreadPoolExecutor(max_workers=max(1, min(len(srcs), os.cpu_count() or 4))) as ex:
-        objs = list(ex.map(lambda s: _compile(s, extra), srcs))
-    tmp = LIB + f".{os.getpid()}.tmp"
+        objs = list(ex.map(lambda s: _compile(s, extra, build_dir), srcs))
+    tmp = lib + f".{os.getpid()}.tmp"
     cmd = ["nvcc", ARCH, "-shared", "-cudart", "static", "-o", tmp, *objs]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed: {' '.join(cmd)}\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
+    os.replace(tmp, lib)
     if verbose:
-        print(f"built {LIB}")
-    return LIB
+        print(f"built {lib}")
+    return lib
 
 
 if __name__ == "__main__":
-    build(force="--force" in sys.argv, verbose=True)
+    build(force="--force" in sys.argv, verbose=True, checked="--checked" in sys.argv)

@@ -325,3 +325,31 @@ const char *fx_status_string(fx_status s) {
 const char *fx_version(void) { return "fx 1.0 sm_103a"; }
 
 }  // extern "C"
+
+namespace fx {
+bool checked_build() {
+#ifdef FX_CHECKED
+  return true;
+#else
+  return false;
+#endif
+}
+}  // namespace fx
+
+extern "C" fx_status fx_checked_violations(uint64_t *count, int32_t reset) {
+  if (!count) return FX_ERR_INVALID_ARG;
+  *count = 0;
+  if (!fx::checked_build()) return FX_ERR_UNSUPPORTED;
+  if (cudaDeviceSynchronize() != cudaSuccess) return FX_ERR_CUDA;
+  unsigned long long (*const readers[])(bool) = {fx::checked_count_stream, fx::checked_count_stream_wide,
+                                                  fx::checked_count_tile, fx::checked_count_plan,
+                                                  fx::checked_count_noalloc, fx::checked_count_hmf};
+  uint64_t total = 0;
+  for (auto r : readers) {
+    const unsigned long long c = r(reset != 0);
+    if (c == ~0ULL) return FX_ERR_CUDA;
+    total += c;
+  }
+  *count = total;
+  return FX_OK;
+}

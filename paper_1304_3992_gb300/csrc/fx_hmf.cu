@@ -23,6 +23,7 @@
 #include <cstdint>
 #include <utility>
 
+#include "fx_checked.cuh"
 #include "fx_internal.h"
 
 namespace fx {
@@ -101,6 +102,7 @@ struct HmfStrip {
   unsigned char *outb_;
   uint32_t pitch32_, opitch32_;
   bool vst_;  // one store of the lane's two output pixels (aligned rows)
+  bool colok_;  // FX_CHECKED: this lane's loaded columns lie in the image
   uint32_t raw0_[L], raw1_[L];  // loaded pixels of the next L rows
   uint32_t win_[K][5];          // per ring row: the pair words shifted by -2..2 columns
 
@@ -114,12 +116,14 @@ struct HmfStrip {
     if constexpr (kPair) {
       const int64_t cb = (c0 < W - 2 ? c0 : W - 2) & ~int64_t{1};  // even pair holding both columns
       p0_ = p1_ = reinterpret_cast<const unsigned char *>(img) + cb * static_cast<int64_t>(sizeof(T));
+      colok_ = cb >= 0 && cb + 1 < W;
       const uint32_t h0 = static_cast<uint32_t>(c0 - cb), h1 = static_cast<uint32_t>(c1 - cb);
       if constexpr (sizeof(T) == 2) sel_ = (h0 ? 0x32u : 0x10u) | ((h1 ? 0x32u : 0x10u) << 8);
       else sel_ = h0 | 0x40u | (h1 << 8) | 0x4000u;
     } else {
       p0_ = reinterpret_cast<const unsigned char *>(img) + c0 * static_cast<int64_t>(sizeof(T));
       p1_ = reinterpret_cast<const unsigned char *>(img) + c1 * static_cast<int64_t>(sizeof(T));
+      colok_ = c0 >= 0 && c0 < W && c1 >= 0 && c1 < W;
       sel_ = 0x5410u;
     }
     // pitches are below 2^32 bytes and sides below 2^30 (checked by the host)
@@ -144,7 +148,8 @@ struct HmfStrip {
   // kAsync: input row Y0 - R + t (clamped) into ring slot t mod kAsyncRows, as
   // one commit group
   __device__ __forceinline__ void issue(int32_t t) {
-    cp_async4(&ring_[t & (kAsyncRows - 1)][lane], q0_ + row_off(t));
+    const int32_t tc = t < tlo_ ? tlo_ : (t > thi_ ? thi_ : t);  // the row row_off reads
+    if (FX_GUARD(colok_ && tc >= tb_ && Y0 - R + tc < H)) cp_async4(&ring_[t & (kAsyncRows - 1)][lane], q0_ + row_off(t));
     cp_async_commit();
   }
 
@@ -152,6 +157,8 @@ struct HmfStrip {
   template <int S>
   __device__ __forceinline__ void load(int32_t t) {
     const uint64_t off = row_off(t);
+    const int32_t tc = t < tlo_ ? tlo_ : (t > thi_ ? thi_ : t);
+    if (!FX_GUARD(colok_ && tc >= tb_ && Y0 - R + tc < H)) return;
     if constexpr (kPair) {
       if constexpr (sizeof(T) == 2) raw0_[S] = __ldg(reinterpret_cast<const uint32_t *>(q0_ + off));
       else raw0_[S] = __ldg(reinterpret_cast<const uint16_t *>(q0_ + off));
@@ -199,6 +206,7 @@ struct HmfStrip {
       h = med3(plus, cross, C[2]);
     }
     if (lane < 1 || lane > 30 || x >= W) return;
+    if (!FX_GUARD(x >= 0 && Y0 + orow < H)) return;
     unsigned char *d = outb_ + static_cast<uint64_t>(static_cast<uint32_t>(orow)) * opitch32_;
     if (vst_ && x + 1 < W) {  // x is even, so the pair is aligned
       if constexpr (sizeof(T) == 2) *reinterpret_cast<uint32_t *>(d) = h;
@@ -297,3 +305,7 @@ extern "C" fx_status fx_hybrid_median(const void *img, int64_t width, int64_t he
                                   static_cast<uint16_t *>(out), out_pitch_bytes, window, s);
   return e == cudaSuccess ? FX_OK : FX_ERR_CUDA;
 }
+
+namespace fx {
+FX_CHECK_COUNTER(checked_count_hmf)
+}  // namespace fx

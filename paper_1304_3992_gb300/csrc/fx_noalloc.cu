@@ -191,3 +191,7 @@ extern "C" fx_status fx_extract_batch_noalloc(const fx_params *params, const fx_
   noalloc_batch_kernel<<<static_cast<unsigned>(sms * 2), gen::NT, smem, s>>>(counter, tab, kp8, kp16);
   return cudaGetLastError() == cudaSuccess ? FX_OK : FX_ERR_CUDA;
 }
+
+namespace fx {
+FX_CHECK_COUNTER(checked_count_noalloc)
+}  // namespace fx

@@ -744,3 +744,7 @@ fx_status fx_extract_host_batch(fx_plan *p, const fx_image_desc *descs, int32_t 
 }
 
 }  // extern "C"
+
+namespace fx {
+FX_CHECK_COUNTER(checked_count_plan)
+}  // namespace fx

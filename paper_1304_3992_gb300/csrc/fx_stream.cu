@@ -77,3 +77,7 @@ cudaError_t launch_fast(const ImageView &v, const KParams &kp, cudaStream_t s) {
 }
 
 }  // namespace fx
+
+namespace fx {
+FX_CHECK_COUNTER(checked_count_stream)
+}  // namespace fx

@@ -44,6 +44,7 @@
 #pragma once
 #include <cstdint>
 
+#include "fx_checked.cuh"
 #include "fx_internal.h"
 
 namespace fx {
@@ -370,6 +371,11 @@ struct Strip {
   // kAsync: shared-memory address of this lane's word in ring slot 4 (k & 1)
   // (slots 4 (k & 1) + S hold the rows of iteration k) and in the other half
   uint32_t ring_h_, ring_o_;
+  // FX_CHECKED: the ring's first slot, and whether this lane's loaded
+  // column(s) lie in the row (the image, or the padding element after column
+  // W - 1 of an odd-width row with pitch slack)
+  uint32_t ring_base_;
+  bool colok_;
 
   __device__ Strip(const ImageView &v_, const KParams &kp_, int64_t x0, int64_t y0, int64_t y1,
                    uint32_t (*words)[32])
@@ -412,6 +418,7 @@ struct Strip {
       const int64_t we = W + (W & 1);
       const int64_t cb = (d0 < we - 2 ? d0 : we - 2) & ~int64_t{1};
       if (cb + 1 >= W) vhi_ = 0;
+      colok_ = cb >= 0 && (cb + 1 < W || (cb + 1 == W && v.pitch >= (W + 1) * static_cast<int64_t>(sizeof(T))));
       p0_ = p1_ = base + cb * static_cast<int64_t>(sizeof(T));
       const uint32_t h0 = static_cast<uint32_t>(d0 - cb), h1 = static_cast<uint32_t>(d1 - cb);
       if constexpr (sizeof(T) == 2) {
@@ -426,13 +433,14 @@ struct Strip {
     } else {
       p0_ = base + d0 * static_cast<int64_t>(sizeof(T));
       p1_ = base + d1 * static_cast<int64_t>(sizeof(T));
+      colok_ = d0 >= 0 && d0 < W && d1 >= 0 && d1 < W;
       sel_ = 0x5410u;
       selb0_ = selb1_ = 0x7410u;  // each load holds one zero-extended pixel
     }
     vmax_ = 0;
     for (int i = 0; i < 12; ++i) acc_[i] = 0;
     for (int i = 0; i < kWords; ++i) sw_[i][lane] = 0;
-    ring_h_ = ring_o_ = static_cast<uint32_t>(__cvta_generic_to_shared(&sw_[kRing][lane]));
+    ring_h_ = ring_o_ = ring_base_ = static_cast<uint32_t>(__cvta_generic_to_shared(&sw_[kRing][lane]));
 #pragma unroll
     for (int s = 0; s < 4; ++s) {
       f_[s] = h1_[s] = h2_[s] = A::zero();
@@ -453,6 +461,7 @@ struct Strip {
   __device__ __forceinline__ void load_row(int32_t tr) {
     const int32_t yr = kClamp ? (tr < rlo ? rlo : (tr > rhi ? rhi : tr)) : tr;
     const uint64_t off = static_cast<uint64_t>(static_cast<uint32_t>(yr - rbase)) * pitch32;
+    if (!FX_GUARD(yr >= rlo && yr <= rhi && yr >= rbase && colok_)) return;
     if constexpr (kPair) {
       if constexpr (sizeof(T) == 2) raw_[S] = __ldg(reinterpret_cast<const uint32_t *>(p0_ + off));
       else raw_[S] = __ldg(reinterpret_cast<const uint16_t *>(p0_ + off));
@@ -468,6 +477,11 @@ struct Strip {
   __device__ __forceinline__ void load_row_async(uint32_t dst, int32_t tr) {
     const int32_t yr = kClamp ? (tr < rlo ? rlo : (tr > rhi ? rhi : tr)) : tr;
     const uint64_t off = static_cast<uint64_t>(static_cast<uint32_t>(yr - rbase)) * pitch32;
+    if (!FX_GUARD(yr >= rlo && yr <= rhi && yr >= rbase && colok_ && dst - ring_base_ < 128u * kRingRows &&
+                  (dst - ring_base_) % 128u == 0)) {
+      asm volatile("cp.async.commit_group;" ::: "memory");  // an empty group keeps the wait counts
+      return;
+    }
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n\tcp.async.commit_group;" ::"r"(dst), "l"(p0_ + off)
                  : "memory");
   }
@@ -531,7 +545,9 @@ struct Strip {
       uint32_t r0, r1;
       if constexpr (kAsync) {
         // row t is in ring slot t & 7 = 4 (k & 1) + S; six younger rows may be in flight
-        asm volatile("cp.async.wait_group 6;\n\tld.shared.u32 %0, [%1];" : "=r"(r0) : "r"(ring_h_ + 128u * S) : "memory");
+        r0 = 0;
+        if (FX_GUARD(ring_h_ + 128u * S - ring_base_ < 128u * kRingRows))
+          asm volatile("cp.async.wait_group 6;\n\tld.shared.u32 %0, [%1];" : "=r"(r0) : "r"(ring_h_ + 128u * S) : "memory");
         r1 = r0;
         // refill the slot of row t - 1 (read one step ago) with row t + 7
         load_row_async<kChk>(S == 0 ? ring_o_ + 384u : ring_h_ + 128u * (S - 1), t + kRingRows - 1);
@@ -857,6 +873,8 @@ struct Strip {
     const uint32_t rows = ((1u << rhi) - 1u) & ~((1u << rlo) - 1u);
     uint8_t *dst = v.out + (ybase - v.y_begin) * v.out_pitch + x;
     const uint32_t op = static_cast<uint32_t>(v.out_pitch);
+    // FX_CHECKED: the rows written lie in the view's output rows, the columns in the image
+    if (!FX_GUARD(x >= 0 && x < W && ybase + rlo >= v.y_begin && ybase + rhi <= v.y_end)) return;
     if (vstore && x + 1 < W) {
       // two rows at a time: their 4 bits (h bits 28-2r .. 31-2r) spread to 4
       // bytes by one multiply, then one 16-bit store per row
@@ -932,6 +950,7 @@ struct Strip {
         sw_[kLev + 2 * l + 1][lane] = a;
         sw_[kLev + 2 * l][lane] = cur;
         const uint32_t h = median(b, a, cur, kp.hmf[l]);
+        if (!FX_GUARD(l < FX_MAX_HMF_LEVELS && kLev + 2 * l + 2 <= kZA)) break;
         cur = l + 1 < nl ? replicate(gm - l - 1, h, sw_[kLev + 2 * l + 2][lane]) : h;
       }
       if (gm - nl >= 0) store(gm - nl, cur);  // the last level's words of block gm - nl
@@ -1061,7 +1080,9 @@ __device__ __forceinline__ void fast_unit(const ImageView &v, const KParams &kp,
   const int64_t Y0 = v.y_begin + uy * uh;
   const int64_t Y1 = Y0 + uh < v.y_end ? Y0 + uh : v.y_end;
   S s(v, kp, X0, Y0, Y1, words);
-  if (!s.template run<kTail>() && (threadIdx.x & 31) == 0) *unit_marker(v, ux, uy, uh, uw) = kRedo;
+  if (!s.template run<kTail>() && (threadIdx.x & 31) == 0 &&
+      FX_GUARD(uy * uh < v.y_end - v.y_begin && ux * uw < v.width))
+    *unit_marker(v, ux, uy, uh, uw) = kRedo;
 }
 
 template <typename T, bool kF32Log, bool kSrcZ, bool kWide = false>
@@ -1071,7 +1092,8 @@ __device__ __forceinline__ void fast_unit_redo(const ImageView &v, const KParams
   constexpr int uw = strip_width(kSrcZ, kWide);
   if (kp.fbound >= 0) {
     uint8_t mark = 0;
-    if ((threadIdx.x & 31) == 0) mark = *unit_marker(v, ux, uy, uh, uw);
+    if ((threadIdx.x & 31) == 0 && FX_GUARD(uy * uh < v.y_end - v.y_begin && ux * uw < v.width))
+      mark = *unit_marker(v, ux, uy, uh, uw);
     if (__shfl_sync(st::kFull, mark, 0) != kRedo) return;
   }
   const int64_t X0 = ux * uw;

@@ -11,3 +11,7 @@ cudaError_t launch_wide(const ImageView &v, const KParams &kp, cudaStream_t s, i
 }
 
 }  // namespace fx
+
+namespace fx {
+FX_CHECK_COUNTER(checked_count_stream_wide)
+}  // namespace fx

@@ -49,3 +49,7 @@ cudaError_t launch_tile_general(const ImageView &v, const KParams &kp, cudaStrea
 }
 
 }  // namespace fx
+
+namespace fx {
+FX_CHECK_COUNTER(checked_count_tile)
+}  // namespace fx

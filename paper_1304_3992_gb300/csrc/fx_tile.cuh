@@ -19,6 +19,7 @@
 #include <cstdint>
 
 #pragma once
+#include "fx_checked.cuh"
 #include "fx_internal.h"
 
 namespace fx {
@@ -63,14 +64,17 @@ template <typename V>
 struct Arr {
   V *p;
   int64_t ox, oy;
-  int w;
+  int w, h;  // columns and rows
   __device__ V &at_clamped(int64_t xc, int64_t yc) const {  // xc, yc already clamped
-    return p[(yc - oy) * w + (xc - ox)];
+    int64_t i = (yc - oy) * w + (xc - ox);
+    if (!FX_GUARD(yc - oy >= 0 && yc - oy < h && xc - ox >= 0 && xc - ox < w)) i = 0;
+    return p[i];
   }
 };
 
 template <typename T>
 __device__ __forceinline__ int32_t load_px(const ImageView &v, int64_t x, int64_t y) {
+  if (!FX_GUARD(y >= v.row0 && y < v.row_lim && x >= 0 && x < v.width)) return 0;
   const uint8_t *row = static_cast<const uint8_t *>(v.img) + (y - v.row0) * v.pitch;
   return static_cast<int32_t>(reinterpret_cast<const T *>(row)[x]);
 }
@@ -136,28 +140,28 @@ __device__ void general_tile(const ImageView &v, const KParams &kp, int64_t x0, 
   const int64_t W = v.width, H = v.height;
 
   unsigned char *cur = smem;
-  Arr<int32_t> I{reinterpret_cast<int32_t *>(cur), x0 - R.i, y0 - R.i, TW + 2 * R.i};
+  Arr<int32_t> I{reinterpret_cast<int32_t *>(cur), x0 - R.i, y0 - R.i, TW + 2 * R.i, TH + 2 * R.i};
   cur += sizeof(int32_t) * area(R.i);
   Arr<int32_t> L[2];
   for (int f = 0; f < 2; ++f) {
-    L[f] = Arr<int32_t>{reinterpret_cast<int32_t *>(cur), x0 - R.l, y0 - R.l, TW + 2 * R.l};
+    L[f] = Arr<int32_t>{reinterpret_cast<int32_t *>(cur), x0 - R.l, y0 - R.l, TW + 2 * R.l, TH + 2 * R.l};
     cur += sizeof(int32_t) * area(R.l);
   }
   Arr<uint8_t> Z[2];
   for (int f = 0; f < 2; ++f) {
-    Z[f] = Arr<uint8_t>{cur, x0 - R.z, y0 - R.z, TW + 2 * R.z};
+    Z[f] = Arr<uint8_t>{cur, x0 - R.z, y0 - R.z, TW + 2 * R.z, TH + 2 * R.z};
     cur += area(R.z);
   }
   Arr<uint8_t> M[2];
   for (int k = 0; k < 2; ++k) {
-    M[k] = Arr<uint8_t>{cur, x0 - R.m, y0 - R.m, TW + 2 * R.m};
+    M[k] = Arr<uint8_t>{cur, x0 - R.m, y0 - R.m, TW + 2 * R.m, TH + 2 * R.m};
     cur += area(R.m);
   }
 
   // a1: one read of the input tile plus halo, clamped to the image.
   for (int i = threadIdx.x; i < area(R.i); i += NT) {
     int64_t x = clampll(I.ox + i % I.w, 0, W - 1), y = clampll(I.oy + i / I.w, 0, H - 1);
-    I.p[i] = load_px<T>(v, x, y);
+    if (FX_GUARD(i < I.w * I.h)) I.p[i] = load_px<T>(v, x, y);
   }
   __syncthreads();
 
@@ -170,8 +174,10 @@ __device__ void general_tile(const ImageView &v, const KParams &kp, int64_t x0, 
         int64_t yy = clampll(yc + dy, 0, H - 1);
         for (int dx = -2; dx <= 2; ++dx) R[ring_index(dx, dy)] += I.at_clamped(clampll(xc + dx, 0, W - 1), yy);
       }
-      L[0].p[i] = __float_as_int(log_f32(kp, 0, R));
-      L[1].p[i] = __float_as_int(log_f32(kp, 1, R));
+      if (FX_GUARD(i < L[0].w * L[0].h)) {
+        L[0].p[i] = __float_as_int(log_f32(kp, 0, R));
+        L[1].p[i] = __float_as_int(log_f32(kp, 1, R));
+      }
       continue;
     }
     int32_t acc0 = 0, acc1 = 0;
@@ -183,8 +189,10 @@ __device__ void general_tile(const ImageView &v, const KParams &kp, int64_t x0, 
         acc1 += kp.w[1][(dy + 2) * 5 + dx + 2] * a;
       }
     }
-    L[0].p[i] = acc0;
-    L[1].p[i] = acc1;
+    if (FX_GUARD(i < L[0].w * L[0].h)) {
+      L[0].p[i] = acc0;
+      L[1].p[i] = acc1;
+    }
   }
   __syncthreads();
 
@@ -210,7 +218,7 @@ __device__ void general_tile(const ImageView &v, const KParams &kp, int64_t x0, 
         } else {
           z = opposite_f(nb[0], nb[1]) || opposite_f(nb[2], nb[3]);
         }
-        Z[f].p[i] = z;
+        if (FX_GUARD(i < Z[f].w * Z[f].h)) Z[f].p[i] = z;
         continue;
       }
       int64_t c = L[f].at_clamped(xc, yc);
@@ -228,7 +236,7 @@ __device__ void general_tile(const ImageView &v, const KParams &kp, int64_t x0, 
       } else {
         z = opposite(nb[0], nb[1]) || opposite(nb[2], nb[3]);
       }
-      Z[f].p[i] = z;
+      if (FX_GUARD(i < Z[f].w * Z[f].h)) Z[f].p[i] = z;
     }
   }
   __syncthreads();
@@ -277,7 +285,7 @@ __device__ void general_tile(const ImageView &v, const KParams &kp, int64_t x0, 
       bool keep = (d5 > kp.tsdmax[f]) ? (d3 > kp.tsd3[f]) : (d5 > kp.tsd5[f]);
       if (keep) m = true;
     }
-    M[0].p[i] = m;
+    if (FX_GUARD(i < M[0].w * M[0].h)) M[0].p[i] = m;
   }
   __syncthreads();
 
@@ -287,7 +295,7 @@ __device__ void general_tile(const ImageView &v, const KParams &kp, int64_t x0, 
   Arr<uint8_t> in = M[0];
   for (int lev = 0; lev < kp.nhmf; ++lev) {
     const int k = kp.hmf[lev], r = k / 2, r_out = r_cur - r;
-    Arr<uint8_t> out{M[src ^ 1].p, x0 - r_out, y0 - r_out, TW + 2 * r_out};
+    Arr<uint8_t> out{M[src ^ 1].p, x0 - r_out, y0 - r_out, TW + 2 * r_out, TH + 2 * r_out};
     for (int i = threadIdx.x; i < area(r_out); i += NT) {
       int64_t xc = clampll(out.ox + i % out.w, 0, W - 1), yc = clampll(out.oy + i / out.w, 0, H - 1);
       int plus = 0, cross = 0;
@@ -302,7 +310,7 @@ __device__ void general_tile(const ImageView &v, const KParams &kp, int64_t x0, 
       }
       int c = in.at_clamped(xc, yc);
       int mp = plus > r * 2, mxv = cross > r * 2;  // majority of 2k-1 = 4r+1 values
-      out.p[i] = (mp + mxv + c) >= 2;
+      if (FX_GUARD(i < out.w * out.h)) out.p[i] = (mp + mxv + c) >= 2;
     }
     __syncthreads();
     src ^= 1;
@@ -313,7 +321,8 @@ __device__ void general_tile(const ImageView &v, const KParams &kp, int64_t x0, 
   // a8: one write of the mask tile.
   for (int i = threadIdx.x; i < TW * TH; i += NT) {
     int64_t x = x0 + i % TW, y = y0 + i / TW;
-    if (x < W && y < v.y_end) v.out[(y - v.y_begin) * v.out_pitch + x] = M[src].p[(i / TW) * TW + i % TW];
+    if (x < W && y < v.y_end && FX_GUARD(x >= 0 && y >= v.y_begin))
+      v.out[(y - v.y_begin) * v.out_pitch + x] = M[src].p[(i / TW) * TW + i % TW];
   }
 }
 

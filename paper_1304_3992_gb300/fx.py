@@ -13,6 +13,8 @@ import threading
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libfx.so")
+# the checked build (every kernel memory index range-checked and counted)
+CHECKED_LIB_PATH = os.path.join(_HERE, "_build_checked", "libfx_checked.so")
 
 FX_U8, FX_U16 = 1, 2
 FX_LOG_INT, FX_LOG_FP32 = 0, 1
@@ -85,6 +87,7 @@ _SIGNATURES = {
     "fx_hybrid_median": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
                                         ctypes.c_int, ctypes.c_int32, ctypes.c_void_p, ctypes.c_int64,
                                         ctypes.c_void_p]),
+    "fx_checked_violations": (ctypes.c_int, [ctypes.POINTER(ctypes.c_uint64), ctypes.c_int32]),
     "fx_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "fx_version": (ctypes.c_char_p, []),
 }
@@ -299,3 +302,15 @@ class Plan:
             arr[i].dtype, arr[i].out_mask, arr[i].out_pitch = dt, out.ctypes.data, out.strides[0]
         _check(self._lib.fx_extract_host_batch(self._h, arr, len(pairs)), "fx_extract_host_batch")
         return [out for _, out in pairs]
+
+
+def checked_violations(reset: bool = False):
+    """Range-check failures counted by the checked build's kernels (None when
+    the loaded library is the normal build)."""
+    n = ctypes.c_uint64(0)
+    code = load().fx_checked_violations(ctypes.byref(n), 1 if reset else 0)
+    if code == 2:  # FX_ERR_UNSUPPORTED: not the checked build
+        return None
+    _check(code, "fx_checked_violations")
+    return int(n.value)
+
