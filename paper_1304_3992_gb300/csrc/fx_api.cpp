@@ -342,6 +342,7 @@ extern "C" fx_status fx_checked_violations(uint64_t *count, int32_t reset) {
   if (!fx::checked_build()) return FX_ERR_UNSUPPORTED;
   if (cudaDeviceSynchronize() != cudaSuccess) return FX_ERR_CUDA;
   unsigned long long (*const readers[])(bool) = {fx::checked_count_stream, fx::checked_count_stream_wide,
+                                                  fx::checked_count_stream_compact,
                                                   fx::checked_count_tile, fx::checked_count_plan,
                                                   fx::checked_count_noalloc, fx::checked_count_hmf};
   uint64_t total = 0;

@@ -95,13 +95,17 @@ cudaError_t launch_tile_general(const ImageView &v, const KParams &kp, cudaStrea
 // FX_CHECKED build; 0 otherwise, ~0 when the counter cannot be read).
 unsigned long long checked_count_stream(bool reset);
 unsigned long long checked_count_stream_wide(bool reset);
+unsigned long long checked_count_stream_compact(bool reset);
 unsigned long long checked_count_tile(bool reset);
 unsigned long long checked_count_plan(bool reset);
 unsigned long long checked_count_noalloc(bool reset);
 unsigned long long checked_count_hmf(bool reset);
 bool checked_build();
-bool fast_path_supported(const KParams &kp);  // the streaming kernels (narrow or wide strips)
-bool stream_narrow(const KParams &kp);        // the narrow strips (also the batched kernels)
+bool fast_path_supported(const KParams &kp);  // the streaming kernels (compact, narrow or wide strips)
+bool stream_narrow(const KParams &kp);        // the narrow strips serve it (also the batched kernels)
+int strip_class(const KParams &kp);           // the smallest strip class that serves kp (its median radius sum)
+cudaError_t launch_compact(const ImageView &v, const KParams &kp, cudaStream_t s, int64_t blocks, int64_t units_x,
+                           int64_t units, int uh);
 cudaError_t launch_wide(const ImageView &v, const KParams &kp, cudaStream_t s, int64_t blocks, int64_t units_x,
                         int64_t units, int uh);
 bool pair_loads_ok(const ImageView &v);

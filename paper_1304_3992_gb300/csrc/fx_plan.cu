@@ -330,7 +330,7 @@ fx_status rebuild(fx_plan *p) {
 fx_status fill_table(fx_plan *p, unsigned char *h, const fx_image_desc *d, int32_t n) {
   BatchHeader *hdr = reinterpret_cast<BatchHeader *>(h);
   BatchImage *ims = reinterpret_cast<BatchImage *>(h + sizeof(BatchHeader));
-  const int uwx = p->fast ? strip_width(p->kp8.source == 1) : gen::TW;  // output columns per unit
+  const int uwx = p->fast ? strip_width(p->kp8.source == 1, kNarrowRm) : gen::TW;  // output columns per unit
   int uh = p->fast ? p->unit_h : gen::TH;
   if (p->fast && p->auto_h) {
     // the wave model of fx_extract over the whole batch: a warp walks uh rows
@@ -443,7 +443,7 @@ fx_status fx_plan_create(fx_plan **out, const fx_params *params, int32_t max_ima
   p->fast = stream_narrow(p->kp8) && stream_narrow(p->kp16);
   p->device = device;
   p->max_images = max_images;
-  p->unit_w = strip_width(p->kp8.source == 1);
+  p->unit_w = strip_width(p->kp8.source == 1, kNarrowRm);
   p->unit_h = kDefaultUnitH;
   p->ctas_per_sm = p->fast ? kFirstPassCtas : 2;
   p->auto_h = true;
@@ -553,7 +553,7 @@ fx_status fx_plan_autotune(fx_plan *p, const fx_image_desc *descs, int32_t n, vo
   fx_status st = FX_OK;
   // candidates: the automatic height (0), then the fixed heights
   for (int c = -1; c < kNumUnitHeights && st == FX_OK; ++c) {
-    const int uw = strip_width(p->kp8.source == 1), uh = c < 0 ? 0 : kUnitHeights[c];
+    const int uw = strip_width(p->kp8.source == 1, kNarrowRm), uh = c < 0 ? 0 : kUnitHeights[c];
     for (int cps = 1; cps <= kMaxCtasPerSm && st == FX_OK; ++cps) {
       if (!p->fast && uh != 0) continue;
       if ((st = fx_plan_set_tile(p, uw, uh, cps)) != FX_OK) break;

@@ -7,11 +7,13 @@
 namespace fx {
 
 // The streaming kernels cover both standard-deviation sources and up to four
-// median passes: narrow strips while the median radii add up to at most 3
-// (halo: 2 LoG + 1 crossing (+ 2 crossing-map deviation) + 3 median columns),
-// wide strips up to 7.  The batched plans use the narrow strips only.
+// median passes: compact strips while the median radii add up to at most 1
+// (halo: 2 LoG + 1 crossing (+ 2 crossing-map deviation) + 1 median column),
+// narrow strips up to 3, wide strips up to 7.  The batched plans use the
+// narrow strips only.
 bool stream_narrow(const KParams &kp) { return kp.nhmf <= FX_MAX_HMF_LEVELS && kp.r_m <= kNarrowRm; }
 bool fast_path_supported(const KParams &kp) { return kp.nhmf <= FX_MAX_HMF_LEVELS && kp.r_m <= kWideRm; }
+int strip_class(const KParams &kp) { return kp.r_m <= kCompactRm ? kCompactRm : kp.r_m <= kNarrowRm ? kNarrowRm : kWideRm; }
 
 // One aligned load per lane and row: base and pitch multiples of two pixels,
 // and an even width or a row pitch with room for one more pixel, so that
@@ -62,8 +64,8 @@ int unit_height(int64_t rows, int64_t units_x, const KParams &kp) {
 }
 
 cudaError_t launch_fast(const ImageView &v, const KParams &kp, cudaStream_t s) {
-  const bool wide = !stream_narrow(kp);
-  const int uw = strip_width(kp.source == 1, wide);
+  const int rm_class = strip_class(kp);
+  const int uw = strip_width(kp.source == 1, rm_class);
   const int64_t units_x = (v.width + uw - 1) / uw;
   const int uh = unit_height(v.y_end - v.y_begin, units_x, kp);
   const int64_t units_y = (v.y_end - v.y_begin + uh - 1) / uh;
@@ -71,9 +73,10 @@ cudaError_t launch_fast(const ImageView &v, const KParams &kp, cudaStream_t s) {
   if (units <= 0) return cudaSuccess;
   const int64_t blocks = (units + kWarpsPerCta - 1) / kWarpsPerCta;
   if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
-  if (wide) return launch_wide(v, kp, s, blocks, units_x, units, uh);
-  return v.elem == 1 ? launch_t<uint8_t, false>(v, kp, s, blocks, units_x, units, uh)
-                     : launch_t<uint16_t, false>(v, kp, s, blocks, units_x, units, uh);
+  if (rm_class == kWideRm) return launch_wide(v, kp, s, blocks, units_x, units, uh);
+  if (rm_class == kCompactRm) return launch_compact(v, kp, s, blocks, units_x, units, uh);
+  return v.elem == 1 ? launch_t<uint8_t, kNarrowRm>(v, kp, s, blocks, units_x, units, uh)
+                     : launch_t<uint16_t, kNarrowRm>(v, kp, s, blocks, units_x, units, uh);
 }
 
 }  // namespace fx

@@ -49,13 +49,14 @@
 
 namespace fx {
 
-// Output columns of a strip: 52, or 48 when the standard deviation is taken
-// over the crossing map (its 5x5 window adds 2 columns to the halo); wide
-// strips (median lists whose radii add up to 4 .. 7) have 4 more halo columns
-// on each side: 44, or 40.
-constexpr int strip_width(bool src_z, bool wide = false) { return (wide ? 44 : 52) - (src_z ? 4 : 0); }
-// Largest sum of median radii of the narrow and the wide strips.
-constexpr int kNarrowRm = 3, kWideRm = 7;
+// Strip classes, by the largest sum of median radii r they serve: compact
+// (r <= 1: no median or one window-3 median), narrow (r <= 3) and wide
+// (r <= 7).  A 64-column window has 3 + r halo columns on each side (2 LoG +
+// 1 crossing + r median), 2 more when the standard deviation is taken over the
+// crossing map (its 5x5 window), so a strip has 58 - 2r output columns: 56, 52
+// or 44 (52, 48 or 40 for the crossing-map source).
+constexpr int kCompactRm = 1, kNarrowRm = 3, kWideRm = 7;
+constexpr int strip_width(bool src_z, int rm_class) { return 58 - 2 * rm_class - (src_z ? 4 : 0); }
 constexpr int kDefaultUnitH = 512;
 // unit heights the batched plan's autotuner times
 constexpr int kNumUnitHeights = 4;
@@ -73,7 +74,7 @@ constexpr int kWarpsPerCta = FX_WARPS_PER_CTA;
 constexpr int kFirstPassCtas = FX_FIRST_PASS_CTAS;
 
 inline bool fast_unit_shape_ok(int w, int h, bool src_z) {
-  return w == strip_width(src_z) && h >= 16 && h <= 8192 && h % 16 == 0;
+  return w == strip_width(src_z, kNarrowRm) && h >= 16 && h <= 8192 && h % 16 == 0;
 }
 inline size_t fast_smem_bytes(int, int, int) { return 0; }  // static shared memory only
 
@@ -308,18 +309,17 @@ struct Ar<kModeF32LogWide> : Ar<kModeF32> {
 // kSd2: the branches have different standard-deviation thresholds (two S words).
 // kSrcZ: the standard deviation is taken over each branch's crossing map
 // (reading R4, source 1) from bit-sliced counts, at block level.
-// kWide: median lists whose radii add up to 4 .. 7 (a wider halo, and the
-// ring prefill one iteration earlier, so that the rows above the unit that the
-// outputs depend on are computed).
-template <typename T, int kMode, bool kPair, bool kSd2, bool kSrcZ, bool kWide = false>
+// kRm: the strip class (kCompactRm, kNarrowRm or kWideRm): the halo, and for
+// the wide class the ring prefill one iteration earlier, so that the rows
+// above the unit that the outputs depend on are computed.
+template <typename T, int kMode, bool kPair, bool kSd2, bool kSrcZ, int kRm = kNarrowRm>
 struct Strip {
   using A = Ar<kMode>;
   // halo columns left of the strip (even: the pair loads are aligned) and
-  // output columns: 2 LoG + 1 crossing (+ 2 standard deviation) + up to 3 (7)
-  // median
-  static constexpr int kLeftHalo = (kWide ? 10 : 6) + (kSrcZ ? 2 : 0), kOutCols = strip_width(kSrcZ, kWide);
-  static_assert(2 * kLeftHalo + kOutCols == 64, "symmetric halo");
-  static constexpr int kK0 = kWide ? -3 : -2;  // first iteration (rows 4 kK0 .. are the ring prefill)
+  // output columns: 2 LoG + 1 crossing (+ 2 standard deviation) + kRm median
+  static constexpr int kLeftHalo = 3 + kRm + (kSrcZ ? 2 : 0), kOutCols = strip_width(kSrcZ, kRm);
+  static_assert(2 * kLeftHalo + kOutCols == 64 && kLeftHalo % 2 == 0, "symmetric, even halo");
+  static constexpr int kK0 = kRm > kNarrowRm ? -3 : -2;  // first iteration (rows 4 kK0 .. are the ring prefill)
   using V = typename A::V;
   using P = typename A::P;
   using Q = typename A::Q;
@@ -938,9 +938,10 @@ struct Strip {
     // of block gm - 1 is stored (the same one block of delay).
     const int nl = kp.nhmf;
     uint32_t cur = m;
-    if (nl <= 1) {  // the default single level (or none) without the level loop
+    if (kRm <= kCompactRm || nl <= 1) {  // a single level (or none) without the level loop
       const uint32_t a = sw_[kLev][lane];
-      if (gm >= 1) store(gm - 1, nl ? median(sw_[kLev + 1][lane], a, m, kp.hmf[0]) : a);
+      // compact strips: the one level is a window-3 median
+      if (gm >= 1) store(gm - 1, nl ? median(sw_[kLev + 1][lane], a, m, kRm <= kCompactRm ? 3 : kp.hmf[0]) : a);
       sw_[kLev + 1][lane] = a;
       sw_[kLev][lane] = m;
     } else {
@@ -1067,15 +1068,15 @@ __device__ __forceinline__ uint32_t (*warp_words(StripWords &w))[32] { return w[
 
 // kF32Log selects the FP32-LoG mode (KParams::f32log) at compile time; kSd2 =
 // !KParams::sd_same (kSd2 = true is correct for any thresholds); kSrcZ =
-// (KParams::source == 1); kWide = median radii adding up to more than 3.
-template <typename T, bool kF32Log, bool kPair, bool kSd2, bool kSrcZ, bool kTail = true, bool kWide = false>
+// (KParams::source == 1); kRm = the strip class.
+template <typename T, bool kF32Log, bool kPair, bool kSd2, bool kSrcZ, bool kTail = true, int kRm = kNarrowRm>
 __device__ __forceinline__ void fast_unit(const ImageView &v, const KParams &kp, int64_t ux, int64_t uy, int,
                                           int uh, uint32_t (*words)[32]) {
   constexpr int kMode = kF32Log ? st::kModeF32Log : st::kModeF32;
-  using S = st::Strip<T, kMode, kPair, kSd2, kSrcZ, kWide>;
+  using S = st::Strip<T, kMode, kPair, kSd2, kSrcZ, kRm>;
   static_assert(S::kWords + S::kRingRows == kStripWords, "shared word layout");
   if (kp.fbound < 0) return;
-  constexpr int uw = strip_width(kSrcZ, kWide);
+  constexpr int uw = strip_width(kSrcZ, kRm);
   const int64_t X0 = ux * uw;
   const int64_t Y0 = v.y_begin + uy * uh;
   const int64_t Y1 = Y0 + uh < v.y_end ? Y0 + uh : v.y_end;
@@ -1085,11 +1086,11 @@ __device__ __forceinline__ void fast_unit(const ImageView &v, const KParams &kp,
     *unit_marker(v, ux, uy, uh, uw) = kRedo;
 }
 
-template <typename T, bool kF32Log, bool kSrcZ, bool kWide = false>
+template <typename T, bool kF32Log, bool kSrcZ, int kRm = kNarrowRm>
 __device__ __forceinline__ void fast_unit_redo(const ImageView &v, const KParams &kp, int64_t ux, int64_t uy,
                                                int, int uh, uint32_t (*words)[32]) {
   constexpr int kMode = kF32Log ? st::kModeF32LogWide : st::kModeInt;
-  constexpr int uw = strip_width(kSrcZ, kWide);
+  constexpr int uw = strip_width(kSrcZ, kRm);
   if (kp.fbound >= 0) {
     uint8_t mark = 0;
     if ((threadIdx.x & 31) == 0 && FX_GUARD(uy * uh < v.y_end - v.y_begin && ux * uw < v.width))
@@ -1099,7 +1100,7 @@ __device__ __forceinline__ void fast_unit_redo(const ImageView &v, const KParams
   const int64_t X0 = ux * uw;
   const int64_t Y0 = v.y_begin + uy * uh;
   const int64_t Y1 = Y0 + uh < v.y_end ? Y0 + uh : v.y_end;
-  st::Strip<T, kMode, false, true, kSrcZ, kWide> s(v, kp, X0, Y0, Y1, words);
+  st::Strip<T, kMode, false, true, kSrcZ, kRm> s(v, kp, X0, Y0, Y1, words);
   s.run();
 }
 

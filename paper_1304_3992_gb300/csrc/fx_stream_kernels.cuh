@@ -1,7 +1,7 @@
 // fx_stream_kernels.cuh -- the streaming kernels and their launch for one
-// strip class (narrow: median radii up to 3; wide: 4 .. 7).  Included by
-// fx_stream.cu (narrow) and fx_stream_wide.cu (wide), so the two classes
-// compile in parallel; every definition has internal linkage.
+// strip class (compact: median radii up to 1; narrow: up to 3; wide: 4 .. 7).
+// Included by fx_stream_compact.cu, fx_stream.cu and fx_stream_wide.cu, so
+// the classes compile in parallel; every definition has internal linkage.
 #pragma once
 #include <cstdint>
 
@@ -12,7 +12,7 @@ namespace {
 
 // The first pass runs 3 CTAs (12 warps) per SM in 168 registers; the redo
 // pass (64-bit sums) runs 2 per SM, where it needs no spill.
-template <typename T, bool kRedoPass, bool kF32Log, bool kPair, bool kSd2, bool kSrcZ, bool kWide>
+template <typename T, bool kRedoPass, bool kF32Log, bool kPair, bool kSd2, bool kSrcZ, int kRm>
 __global__ void __launch_bounds__(32 * kWarpsPerCta, kRedoPass ? 2 : kFirstPassCtas) stream_kernel(const __grid_constant__ ImageView v,
                                                                   const __grid_constant__ KParams kp,
                                                                   int64_t units_x, int64_t units, int uh) {
@@ -20,42 +20,42 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta, kRedoPass ? 2 : kFirstPassC
   const int64_t unit = static_cast<int64_t>(blockIdx.x) * kWarpsPerCta + (threadIdx.x >> 5);
   if (unit >= units) return;  // whole warps only
   if constexpr (kRedoPass)
-    fast_unit_redo<T, kF32Log, kSrcZ, kWide>(v, kp, unit % units_x, unit / units_x, 0, uh, warp_words(words));
+    fast_unit_redo<T, kF32Log, kSrcZ, kRm>(v, kp, unit % units_x, unit / units_x, 0, uh, warp_words(words));
   else
-    fast_unit<T, kF32Log, kPair, kSd2, kSrcZ, true, kWide>(v, kp, unit % units_x, unit / units_x, 0, uh,
+    fast_unit<T, kF32Log, kPair, kSd2, kSrcZ, true, kRm>(v, kp, unit % units_x, unit / units_x, 0, uh,
                                                             warp_words(words));
 }
 
-template <typename T, bool kF32Log, bool kPair, bool kWide>
+template <typename T, bool kF32Log, bool kPair, int kRm>
 void launch_first(const ImageView &v, const KParams &kp, cudaStream_t s, unsigned g, int64_t units_x,
                   int64_t units, int uh) {
   constexpr int nt = 32 * kWarpsPerCta;
-  if (kp.source == 1) stream_kernel<T, false, kF32Log, kPair, false, true, kWide><<<g, nt, 0, s>>>(v, kp, units_x, units, uh);
-  else if (kp.sd_same) stream_kernel<T, false, kF32Log, kPair, false, false, kWide><<<g, nt, 0, s>>>(v, kp, units_x, units, uh);
-  else stream_kernel<T, false, kF32Log, kPair, true, false, kWide><<<g, nt, 0, s>>>(v, kp, units_x, units, uh);
+  if (kp.source == 1) stream_kernel<T, false, kF32Log, kPair, false, true, kRm><<<g, nt, 0, s>>>(v, kp, units_x, units, uh);
+  else if (kp.sd_same) stream_kernel<T, false, kF32Log, kPair, false, false, kRm><<<g, nt, 0, s>>>(v, kp, units_x, units, uh);
+  else stream_kernel<T, false, kF32Log, kPair, true, false, kRm><<<g, nt, 0, s>>>(v, kp, units_x, units, uh);
 }
 
-template <typename T, bool kF32Log, bool kWide>
+template <typename T, bool kF32Log, int kRm>
 void launch_mode(const ImageView &v, const KParams &kp, cudaStream_t s, int64_t blocks, int64_t units_x,
                  int64_t units, int uh) {
   const unsigned g = static_cast<unsigned>(blocks);
   constexpr int nt = 32 * kWarpsPerCta;
   if (kp.fbound >= 0) {
-    if (pair_loads_ok(v)) launch_first<T, kF32Log, true, kWide>(v, kp, s, g, units_x, units, uh);
-    else launch_first<T, kF32Log, false, kWide>(v, kp, s, g, units_x, units, uh);
+    if (pair_loads_ok(v)) launch_first<T, kF32Log, true, kRm>(v, kp, s, g, units_x, units, uh);
+    else launch_first<T, kF32Log, false, kRm>(v, kp, s, g, units_x, units, uh);
   }
   // the second pass recomputes the strips the first one marked (all when fbound < 0)
   if (kp.fbound < 0 || kp.fbound < (sizeof(T) == 1 ? 255 : 65535)) {
-    if (kp.source == 1) stream_kernel<T, true, kF32Log, false, true, true, kWide><<<g, nt, 0, s>>>(v, kp, units_x, units, uh);
-    else stream_kernel<T, true, kF32Log, false, true, false, kWide><<<g, nt, 0, s>>>(v, kp, units_x, units, uh);
+    if (kp.source == 1) stream_kernel<T, true, kF32Log, false, true, true, kRm><<<g, nt, 0, s>>>(v, kp, units_x, units, uh);
+    else stream_kernel<T, true, kF32Log, false, true, false, kRm><<<g, nt, 0, s>>>(v, kp, units_x, units, uh);
   }
 }
 
-template <typename T, bool kWide>
+template <typename T, int kRm>
 cudaError_t launch_t(const ImageView &v, const KParams &kp, cudaStream_t s, int64_t blocks, int64_t units_x,
                      int64_t units, int uh) {
-  if (kp.f32log) launch_mode<T, true, kWide>(v, kp, s, blocks, units_x, units, uh);
-  else launch_mode<T, false, kWide>(v, kp, s, blocks, units_x, units, uh);
+  if (kp.f32log) launch_mode<T, true, kRm>(v, kp, s, blocks, units_x, units, uh);
+  else launch_mode<T, false, kRm>(v, kp, s, blocks, units_x, units, uh);
   return cudaGetLastError();
 }
 

@@ -6,8 +6,8 @@ namespace fx {
 
 cudaError_t launch_wide(const ImageView &v, const KParams &kp, cudaStream_t s, int64_t blocks, int64_t units_x,
                         int64_t units, int uh) {
-  return v.elem == 1 ? launch_t<uint8_t, true>(v, kp, s, blocks, units_x, units, uh)
-                     : launch_t<uint16_t, true>(v, kp, s, blocks, units_x, units, uh);
+  return v.elem == 1 ? launch_t<uint8_t, kWideRm>(v, kp, s, blocks, units_x, units, uh)
+                     : launch_t<uint16_t, kWideRm>(v, kp, s, blocks, units_x, units, uh);
 }
 
 }  // namespace fx

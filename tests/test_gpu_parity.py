@@ -79,11 +79,15 @@ def test_ragged_sizes(cuda_lib, shape, bits):
         assert_same(run(cuda_lib, img, p), oracle.extract(img, d), f"{shape} bits={bits} hmf={hmf}")
 
 
-@pytest.mark.parametrize("w", [1, 2, 31, 32, 33, 63, 64, 65, 95, 127, 129, 191, 257])
-def test_widths_mod_tile(cuda_lib, w):
+@pytest.mark.parametrize("hmf", [(5,), (3,)])
+@pytest.mark.parametrize("w", [1, 2, 31, 32, 33, 51, 52, 53, 55, 56, 57, 63, 64, 65, 95, 103, 104, 105, 111, 112,
+                               113, 127, 129, 191, 257])
+def test_widths_mod_tile(cuda_lib, w, hmf):
+    """Widths around multiples of the narrow (52-column, median 5) and compact
+    (56-column, median 3) strips and of the warp's 64-column window."""
     img = scenes.scene(w + 10, 90, seed=w, n_rects=10, noise_sigma=24, impulse_frac=0.005, bits=12)[:, 5:5 + w].copy()
-    d, p = pair(16.0)
-    assert_same(run(cuda_lib, img, p), oracle.extract(img, d), f"width {w}")
+    d, p = pair(16.0, hmf=hmf)
+    assert_same(run(cuda_lib, img, p), oracle.extract(img, d), f"width {w} hmf {hmf}")
 
 
 @pytest.mark.parametrize("pitch_extra", [0, 2, 256, 1000])
@@ -215,6 +219,23 @@ def test_band16384_u16_unit_seams_all_bands(cuda_lib):
         got = run(cuda_lib, band, p)
         for y0, y1 in fullsize.seam_bands(band.shape[0], uh, seed=b):
             assert_same(got[y0:y1], oracle.extract(band, d, rows=(y0, y1)), f"band {b} rows {y0}:{y1}")
+
+
+@pytest.mark.parametrize("hmf", [(3,), ()])
+def test_band16384_u16_compact_strips_seams(cuda_lib, hmf):
+    """Band 0 of the benchmark with a window-3 median or none, which run on the
+    compact strips (56 output columns): 40-row bands across the first three
+    unit seams of that launch, the top and bottom rows and one random band,
+    and the left and right image borders over a tall band, against the
+    oracle."""
+    import fullsize
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    uh = fullsize.unit_height(16384, 16384, sms, r_m=1)
+    d, p = pair(16.0, hmf=hmf)
+    band = next(iter(scenes.ms_bands_u16_12bit()))
+    got = run(cuda_lib, band, p)
+    for y0, y1 in fullsize.seam_bands(band.shape[0], uh, seed=5):
+        assert_same(got[y0:y1], oracle.extract(band, d, rows=(y0, y1)), f"hmf {hmf} rows {y0}:{y1}")
 
 
 def test_config4_batch_full_size_sampled(cuda_lib):
