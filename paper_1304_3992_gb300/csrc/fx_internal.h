@@ -109,6 +109,7 @@ cudaError_t launch_compact(const ImageView &v, const KParams &kp, cudaStream_t s
 cudaError_t launch_wide(const ImageView &v, const KParams &kp, cudaStream_t s, int64_t blocks, int64_t units_x,
                         int64_t units, int uh);
 bool pair_loads_ok(const ImageView &v);
+bool pair_loads_ok(const void *img, int64_t width, int64_t pitch, int64_t elem);
 cudaError_t launch_fast(const ImageView &v, const KParams &kp, cudaStream_t s);
 cudaError_t launch_extract(const ImageView &v, const KParams &kp, cudaStream_t s);
 

@@ -361,10 +361,7 @@ fx_status fill_table(fx_plan *p, unsigned char *h, const fx_image_desc *d, int32
   for (int32_t i = 0; i < n; ++i) {
     const int64_t op = d[i].out_pitch ? d[i].out_pitch : d[i].width;
     const int64_t elem = d[i].dtype == FX_U8 ? 1 : 2;
-    // the load-path rule of pair_loads_ok (fx_stream.cu)
-    const bool pair = p->fast && reinterpret_cast<uintptr_t>(d[i].img) % (2 * elem) == 0 &&
-                      d[i].pitch_bytes % (2 * elem) == 0 &&
-                      (d[i].width % 2 == 0 || d[i].pitch_bytes >= (d[i].width + 1) * elem);
+    const bool pair = p->fast && pair_loads_ok(d[i].img, d[i].width, d[i].pitch_bytes, elem);
     if (p->fast && group_of(pair, static_cast<int>(elem)) != pass) continue;
     fx_status st = check_image(d[i].img, d[i].width, d[i].height, d[i].pitch_bytes, d[i].dtype,
                                d[i].out_mask, op);

@@ -15,17 +15,21 @@ bool stream_narrow(const KParams &kp) { return kp.nhmf <= FX_MAX_HMF_LEVELS && k
 bool fast_path_supported(const KParams &kp) { return kp.nhmf <= FX_MAX_HMF_LEVELS && kp.r_m <= kWideRm; }
 int strip_class(const KParams &kp) { return kp.r_m <= kCompactRm ? kCompactRm : kp.r_m <= kNarrowRm ? kNarrowRm : kWideRm; }
 
-// One aligned load per lane and row: base and pitch multiples of two pixels,
-// and an even width or a row pitch with room for one more pixel, so that
+// One aligned load per lane and row: base and pitch multiples of 4 bytes.
+// uint16: an even width or a row pitch with room for one more pixel, so that
 // every lane's clamped columns lie in one aligned pair (for an odd width the
 // last column's pair also holds the first padding element, which is never
-// used; the pair is one aligned load that contains an image element, so it
-// stays within the page of that element).
-bool pair_loads_ok(const ImageView &v) {
-  const int64_t two = 2 * static_cast<int64_t>(v.elem);
-  return reinterpret_cast<uintptr_t>(v.img) % two == 0 && v.pitch % two == 0 &&
-         (v.width % 2 == 0 || v.pitch >= (v.width + 1) * v.elem);
+// used).  uint8: each lane loads the aligned 4-byte word holding its pair, so
+// the row pitch reaches the end of the word that holds the last pair.  Every
+// such load starts inside the row, so it stays within the page of an image
+// element.
+bool pair_loads_ok(const void *img, int64_t width, int64_t pitch, int64_t elem) {
+  if (reinterpret_cast<uintptr_t>(img) % 4 != 0 || pitch % 4 != 0) return false;
+  if (elem == 2) return width % 2 == 0 || pitch >= (width + 1) * elem;
+  const int64_t pair_end = width + (width & 1);  // one past the last pair
+  return pitch >= (pair_end + 3) / 4 * 4;
 }
+bool pair_loads_ok(const ImageView &v) { return pair_loads_ok(v.img, v.width, v.pitch, v.elem); }
 
 // Resident warps of the streaming kernel on the current device (3 CTAs of 4
 // warps per SM), cached per device.
@@ -64,6 +68,9 @@ int unit_height(int64_t rows, int64_t units_x, const KParams &kp) {
 }
 
 cudaError_t launch_fast(const ImageView &v, const KParams &kp, cudaStream_t s) {
+  // units start at multiples of 16 rows past y_begin; the top-border
+  // replication of the block logic needs every start at row 0 or >= 19
+  if (v.y_begin != 0 && v.y_begin < 19) return cudaErrorInvalidValue;
   const int rm_class = strip_class(kp);
   const int uw = strip_width(kp.source == 1, rm_class);
   const int64_t units_x = (v.width + uw - 1) / uw;

@@ -353,10 +353,11 @@ struct Strip {
   uint32_t (*sw_)[32];
   static constexpr int kBlk = 0, kPneg = 12, kPpos = 14, kPsS = 16, kLev = 18, kMA = kLev, kZA = 26, kZB = 28,
                        kPcf = 30, kWords = 32;
-  // kAsync (uint16 pixel pairs on the FP32 paths): the input rows arrive in an
-  // 8-row ring of words in shared memory (kRing .. kRing + 7), filled by
-  // cp.async seven rows ahead, so loads in flight hold no registers.
-  static constexpr bool kAsync = sizeof(T) == 2 && kPair && A::kBiased;
+  // kAsync (pixel pairs on the FP32 paths): the input rows arrive in an 8-row
+  // ring of words in shared memory (kRing .. kRing + 7), filled by cp.async
+  // seven rows ahead, so loads in flight hold no registers.  A lane's word is
+  // its uint16 pair, or for uint8 the aligned 4-byte word holding its pair.
+  static constexpr bool kAsync = kPair && A::kBiased;
   static constexpr int kRing = kWords, kRingRows = 8;
   __device__ __forceinline__ uint32_t &blk(int i) { return sw_[kBlk + i][lane]; }
 
@@ -418,9 +419,13 @@ struct Strip {
       const int64_t we = W + (W & 1);
       const int64_t cb = (d0 < we - 2 ? d0 : we - 2) & ~int64_t{1};
       if (cb + 1 >= W) vhi_ = 0;
-      colok_ = cb >= 0 && (cb + 1 < W || (cb + 1 == W && v.pitch >= (W + 1) * static_cast<int64_t>(sizeof(T))));
-      p0_ = p1_ = base + cb * static_cast<int64_t>(sizeof(T));
-      const uint32_t h0 = static_cast<uint32_t>(d0 - cb), h1 = static_cast<uint32_t>(d1 - cb);
+      // the loaded word: the pair itself (uint16), or the aligned 4-byte word
+      // holding it (uint8; the row pitch reaches the end of that word)
+      const int64_t ca = sizeof(T) == 1 ? (cb & ~int64_t{3}) : cb;
+      colok_ = cb >= 0 && (cb + 1 < W || (cb + 1 == W && v.pitch >= (W + 1) * static_cast<int64_t>(sizeof(T)))) &&
+               (sizeof(T) == 2 || ca + 4 <= v.pitch);
+      p0_ = p1_ = base + ca * static_cast<int64_t>(sizeof(T));
+      const uint32_t h0 = static_cast<uint32_t>(d0 - ca), h1 = static_cast<uint32_t>(d1 - ca);
       if constexpr (sizeof(T) == 2) {
         sel_ = (h0 ? 0x32u : 0x10u) | ((h1 ? 0x32u : 0x10u) << 8);
         selb0_ = h0 ? 0x7432u : 0x7410u;
@@ -463,8 +468,7 @@ struct Strip {
     const uint64_t off = static_cast<uint64_t>(static_cast<uint32_t>(yr - rbase)) * pitch32;
     if (!FX_GUARD(yr >= rlo && yr <= rhi && yr >= rbase && colok_)) return;
     if constexpr (kPair) {
-      if constexpr (sizeof(T) == 2) raw_[S] = __ldg(reinterpret_cast<const uint32_t *>(p0_ + off));
-      else raw_[S] = __ldg(reinterpret_cast<const uint16_t *>(p0_ + off));
+      raw_[S] = __ldg(reinterpret_cast<const uint32_t *>(p0_ + off));  // the lane's word (see kAsync)
     } else {
       raw_[S] = __ldg(reinterpret_cast<const T *>(p0_ + off));
       raw1_[S] = __ldg(reinterpret_cast<const T *>(p1_ + off));
@@ -487,6 +491,19 @@ struct Strip {
   }
   __device__ __forceinline__ void async_drain() {
     if constexpr (kAsync) asm volatile("cp.async.wait_group 0;" ::: "memory");
+  }
+
+  // Running maximum of the loaded values (the FP32 bound check): per 16-bit
+  // half for uint16 words, per byte for uint8 (a word may hold the
+  // neighbouring lane's pair too, which only makes the check conservative).
+  __device__ __forceinline__ void track_max(uint32_t w) {
+    vmax_ = sizeof(T) == 1 ? __vmaxu4(vmax_, w) : __vmaxu2(vmax_, w);
+  }
+  __device__ __forceinline__ uint32_t tracked_max() const {
+    if constexpr (sizeof(T) == 1)
+      return max(max(vmax_ & 0xFFu, (vmax_ >> 8) & 0xFFu), max((vmax_ >> 16) & 0xFFu, vmax_ >> 24));
+    else
+      return max(vmax_ & 0xFFFFu, (vmax_ >> 16) & vhi_);
   }
 
   // The lane's two pixels of the row in slot S as a 16-bit pair (column 0 low).
@@ -557,7 +574,7 @@ struct Strip {
       }
       const uint32_t b2 = __byte_perm(r0, 0x4B000000u, selb0_);
       const uint32_t b3 = __byte_perm(kPair ? r0 : r1, 0x4B000000u, selb1_);
-      if (check) vmax_ = __vmaxu2(vmax_, kPair ? r0 : __byte_perm(r0, r1, 0x5410));
+      if (check) track_max(kPair ? r0 : __byte_perm(r0, r1, 0x5410));
       if constexpr (!kAsync) load_row<S, kChk>(t + 4);
       const uint32_t b0 = __shfl_up_sync(kFull, b2, 1), b1 = __shfl_up_sync(kFull, b3, 1);
       const uint32_t b4 = __shfl_down_sync(kFull, b2, 1), b5 = __shfl_down_sync(kFull, b3, 1);
@@ -575,7 +592,7 @@ struct Strip {
     } else {
       const uint32_t w = pixels<S>();
       load_row<S, kChk>(t + 4);  // four rows ahead, into the slot just read
-      if (check) vmax_ = __vmaxu2(vmax_, w);
+      if (check) track_max(w);
       const uint32_t hl = __shfl_up_sync(kFull, w, 1);    // columns -2, -1
       const uint32_t hr = __shfl_down_sync(kFull, w, 1);  // columns 2, 3
       const uint32_t u[6] = {hl & 0xFFFFu, hl >> 16, w & 0xFFFFu, w >> 16, hr & 0xFFFFu, hr >> 16};
@@ -809,7 +826,11 @@ struct Strip {
 
   // Replicated borders of a binary stage (reading R2) for block b: rows above
   // row 0 / below row H - 1 and columns outside the image take the nearest
-  // image pixel's bit (prev: the stage's word of block b - 1).
+  // image pixel's bit (prev: the stage's word of block b - 1).  A unit starts
+  // at row 0 or at a row >= 16 (its start is a multiple of the unit height,
+  // itself a multiple of 16, past the view's first row, which is 0 or >= 64),
+  // so a block that reaches above row 0 starts at row -3 or lies wholly above
+  // the image, where it feeds no output.
   __device__ __forceinline__ uint32_t replicate(int64_t b, uint32_t m, uint32_t prev) {
     const int64_t r0 = Y0 - 3 + 16 * b;  // image row of bit-row 0
     if (r0 < 0) {  // top: rows -3..-1 take row 0 (bit-row 3)
@@ -901,8 +922,7 @@ struct Strip {
   // End of the 16 steps of group g: block g is packed in acc_.
   __device__ __forceinline__ bool end_group(int64_t g) {
     if (check) {
-      const uint32_t m = max(vmax_ & 0xFFFFu, (vmax_ >> 16) & vhi_);
-      if (__any_sync(kFull, m > static_cast<uint32_t>(kp.fbound))) return false;
+      if (__any_sync(kFull, tracked_max() > static_cast<uint32_t>(kp.fbound))) return false;
     }
     uint32_t m = 0;
     int64_t gm;  // block index of m (the mask M)

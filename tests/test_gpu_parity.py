@@ -124,6 +124,30 @@ def test_odd_width_pair_and_fallback_loads(cuda_lib, bits):
             assert_same(run(cuda_lib, buf[:, :w], p), ref, f"{h}x{w} pitch {pitch}")
 
 
+@pytest.mark.parametrize("w", [330, 331, 332, 333])
+def test_uint8_word_loads(cuda_lib, w):
+    """uint8 rows are read as the aligned 4-byte word holding each lane's
+    pair when the base and pitch are multiples of 4 and the pitch reaches the
+    end of the word holding the last pair; otherwise pixel by pixel.  Widths
+    of every residue mod 4 with tight pitch, the smallest pitch that allows the
+    word loads, a 256-byte pitch, and a base two bytes past an aligned address
+    (the padding holds 255, which must not reach the mask), on images taller
+    than one work unit, against the oracle."""
+    from paper_1304_3992_gb300 import fx
+    h = 901
+    img = scenes.scene(w, h, seed=w, n_rects=h * w // 500, noise_sigma=4.0, impulse_frac=0.005, bits=8)
+    d, p = pair(1.0, dtype_code=fx.FX_U8)
+    ref = oracle.extract(img, d)
+    assert ref.sum() > 0
+    assert_same(run(cuda_lib, img, p), ref, f"{w} packed")
+    word = ((w + (w & 1) + 3) // 4) * 4
+    for pitch, off in ((word, 0), (256 * ((w + 255) // 256), 0), (word + 4, 2)):
+        buf = torch.full((h, pitch + off), 255, dtype=torch.uint8, device="cuda")
+        view = buf[:, off:off + w]
+        view.copy_(dev(img))
+        assert_same(run(cuda_lib, view, p), ref, f"{w} pitch {pitch} offset {off}")
+
+
 def test_pitched_output(cuda_lib):
     img = scenes.scene(150, 60, seed=4, n_rects=8, noise_sigma=4, impulse_frac=0.01, bits=8)
     d, p = pair(1.0)
