@@ -188,8 +188,10 @@ typedef struct {
  * Many images of uneven sizes and mixed dtypes in ONE replay of a CUDA graph:
  * persistent kernels pop work units from a tile queue (one kernel per load
  * path and pixel type on the streaming path, then the redo pass), the batched
- * form of Sec. 6.2.2's one-thread-per-pixel mapping.  Each image's mask is byte-identical to
- * fx_extract's.  descs is a HOST array of n descriptors, validated like
+ * form of Sec. 6.2.2's one-thread-per-pixel mapping.  Median lists whose radii
+ * add up to at most 7 run on the streaming strips of fx_extract (compact,
+ * narrow or wide), longer lists on the general tile kernel.  Each image's
+ * mask is byte-identical to fx_extract's.  descs is a HOST array of n descriptors, validated like
  * fx_extract's arguments; the table is copied before the call returns.
  * Output masks must not overlap each other or any input.
  * The plan holds two descriptor tables and two sets of queue counters and
@@ -206,8 +208,10 @@ fx_status fx_extract_batch(fx_plan *plan, const fx_image_desc *descs, int32_t n,
 /*
  * Work-unit shape of the batched kernel and its CTAs per SM.  A unit is a
  * strip of tile_w output columns by tile_h output rows walked by one warp;
- * tile_w must be the strip width of the streaming kernel (52, or 48 when the
- * standard deviation is taken over the crossing map) and tile_h a multiple
+ * tile_w must be the strip width of the plan's streaming strips: 56 with no
+ * median or one window-3 median, 52 while the median radii add up to at most
+ * 3 (the default window 5 included), 44 up to 7; 4 fewer when the standard
+ * deviation is taken over the crossing map.  tile_h is a multiple
  * of 16 in [16, 8192], or 0; ctas_per_sm is in 1..8 (4 warps per CTA).
  * A new plan picks the unit height for each batch itself (multiples of 16 up
  * to 1024, from the batch's unit count against the resident warps; 3 CTAs

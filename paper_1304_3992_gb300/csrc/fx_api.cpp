@@ -336,6 +336,12 @@ bool checked_build() {
 }
 }  // namespace fx
 
+namespace fx {
+// check counters of the batched path's compact and wide kernels (fx_plan_compact.cu, fx_plan_wide.cu)
+unsigned long long checked_count_plan_compact(bool reset);
+unsigned long long checked_count_plan_wide(bool reset);
+}  // namespace fx
+
 extern "C" fx_status fx_checked_violations(uint64_t *count, int32_t reset) {
   if (!count) return FX_ERR_INVALID_ARG;
   *count = 0;
@@ -343,7 +349,7 @@ extern "C" fx_status fx_checked_violations(uint64_t *count, int32_t reset) {
   if (cudaDeviceSynchronize() != cudaSuccess) return FX_ERR_CUDA;
   unsigned long long (*const readers[])(bool) = {fx::checked_count_stream, fx::checked_count_stream_wide,
                                                   fx::checked_count_stream_compact,
-                                                  fx::checked_count_tile, fx::checked_count_plan,
+                                                  fx::checked_count_tile, fx::checked_count_plan, fx::checked_count_plan_compact, fx::checked_count_plan_wide,
                                                   fx::checked_count_noalloc, fx::checked_count_hmf};
   uint64_t total = 0;
   for (auto r : readers) {

@@ -9,60 +9,12 @@
 #include <vector>
 
 #include "fx_internal.h"
+#include "fx_plan_kernels.cuh"
 #include "fx_stream.cuh"
 #include "fx_tile.cuh"
 
 namespace fx {
 namespace {
-
-struct BatchImage {
-  const void *img;
-  int64_t width, height, pitch;
-  uint8_t *out;
-  int64_t out_pitch;
-  int64_t units_x;     // work units across the image
-  int64_t unit_begin;  // first queue index of this image
-  int32_t elem;
-  int32_t pad;
-};
-
-// Streaming path: the queue holds four groups of images, in this order: read
-// with one aligned load per lane (uint16, uint8), then pixel by pixel (uint16,
-// uint8).  Group g owns the units [group_end[g-1], group_end[g]) (group_end[-1]
-// = 0) and runs in a kernel of its own.
-constexpr int kGroups = 4;
-__host__ __device__ constexpr int group_of(bool pair, int elem) { return (pair ? 0 : 2) + (elem == 1 ? 1 : 0); }
-
-struct BatchHeader {
-  int64_t total_units;
-  int64_t group_end[kGroups];  // streaming path only
-  int32_t n;
-  int32_t unit_w, unit_h;  // unit shape in output pixels
-  int32_t pad;
-};
-
-size_t table_bytes(int max_images) { return sizeof(BatchHeader) + sizeof(BatchImage) * max_images; }
-
-// Status bits written by the batch kernel.
-constexpr int kStatusBadDescriptor = 1;
-
-// Persistent kernels: CTAs (general tile) or warps (streaming strip) pop work
-// units -- one output tile / strip segment of one image -- from a global
-// counter until the queue is empty.  Units of different images and dtypes
-// interleave freely; the image is found by binary search over unit offsets.
-__device__ __forceinline__ int find_image(const BatchImage *ims, int n, long long u) {
-  int lo = 0, hi = n - 1;  // last image whose first unit is <= u
-  while (lo < hi) {
-    int mid = (lo + hi + 1) >> 1;
-    if (ims[mid].unit_begin <= u) lo = mid;
-    else hi = mid - 1;
-  }
-  return lo;
-}
-
-__device__ __forceinline__ ImageView view_of(const BatchImage &b) {
-  return ImageView{b.img, b.width, b.height, b.pitch, 0, b.elem, b.out, b.out_pitch, 0, b.height, b.height};
-}
 
 __global__ void __launch_bounds__(256) batch_kernel_general(const unsigned char *table,
                                                             unsigned long long *counter, int *status,
@@ -93,98 +45,28 @@ __global__ void __launch_bounds__(256) batch_kernel_general(const unsigned char 
   }
 }
 
-// One group of the streaming path (load path kPair, pixel type T): its units
-// from counter[g].  Each group is a kernel of its own, so a kernel holds one
-// strip loop (the register allocation and instruction working set of the
-// single-image kernel).
-template <typename T, bool kF32Log, bool kPair, bool kSd2, bool kSrcZ>
-__global__ void __launch_bounds__(32 * kWarpsPerCta, kFirstPassCtas) batch_kernel_fast(const unsigned char *table,
-                                                                      unsigned long long *counter, int *status,
-                                                                      const __grid_constant__ KParams kp) {
-  __shared__ StripWords words;
-  constexpr int g = group_of(kPair, sizeof(T));
-  const BatchHeader *hdr = reinterpret_cast<const BatchHeader *>(table);
-  const BatchImage *ims = reinterpret_cast<const BatchImage *>(table + sizeof(BatchHeader));
-  const long long first = g == 0 ? 0 : hdr->group_end[g - 1];
-  const long long end = hdr->group_end[g];
-  const int lane = threadIdx.x & 31;
-  for (;;) {
-    unsigned long long got = 0;
-    if (lane == 0) got = atomicAdd(counter + g, 1ULL);
-    const long long u = first + static_cast<long long>(__shfl_sync(0xffffffffu, got, 0));
-    if (u >= end) break;
-    const BatchImage &b = ims[find_image(ims, hdr->n, u)];
-    if (b.units_x <= 0 || b.elem != static_cast<int32_t>(sizeof(T))) {
-      if (lane == 0) atomicOr(status, kStatusBadDescriptor);
-      continue;
-    }
-    const ImageView v = view_of(b);
-    const long long local = u - b.unit_begin;
-    const int64_t ux = local % b.units_x, uy = local / b.units_x;
-    fast_unit<T, kF32Log, kPair, kSd2, kSrcZ, false>(v, kp, ux, uy, hdr->unit_w, hdr->unit_h, warp_words(words));
-  }
-}
-
-// Second pass of the streaming path: every warp walks the units with a static
-// stride and recomputes, on the integer (or wide FP32-LoG) path, the strips
-// the first pass marked.  2 CTAs per SM (no spill of the 64-bit sums); the
-// graph launches exactly the resident CTAs, so no CTA waits for a second wave
-// with its share of the stride.
-template <bool kF32Log, bool kSrcZ>
-__global__ void __launch_bounds__(32 * kWarpsPerCta, 2) batch_kernel_redo(const unsigned char *table,
-                                                                      unsigned long long *, int *,
-                                                                      const __grid_constant__ KParams kp8,
-                                                                      const __grid_constant__ KParams kp16) {
-  __shared__ StripWords words;
-  const BatchHeader *hdr = reinterpret_cast<const BatchHeader *>(table);
-  const BatchImage *ims = reinterpret_cast<const BatchImage *>(table + sizeof(BatchHeader));
-  const long long total = hdr->total_units;
-  const long long warps = static_cast<long long>(gridDim.x) * kWarpsPerCta;
-  for (long long u = static_cast<long long>(blockIdx.x) * kWarpsPerCta + (threadIdx.x >> 5); u < total; u += warps) {
-    const BatchImage &b = ims[find_image(ims, hdr->n, u)];
-    if (b.units_x <= 0 || (b.elem != 1 && b.elem != 2)) continue;
-    const ImageView v = view_of(b);
-    const long long local = u - b.unit_begin;
-    const int64_t ux = local % b.units_x, uy = local / b.units_x;
-    if (b.elem == 1) {
-      if (kp8.fbound < 0 || kp8.fbound < 255)
-        fast_unit_redo<uint8_t, kF32Log, kSrcZ>(v, kp8, ux, uy, hdr->unit_w, hdr->unit_h, warp_words(words));
-    } else {
-      fast_unit_redo<uint16_t, kF32Log, kSrcZ>(v, kp16, ux, uy, hdr->unit_w, hdr->unit_h, warp_words(words));
-    }
-  }
-}
-
-// The streaming kernel of group g for a plan's parameters (LoG mode,
-// standard-deviation source and thresholds).
-template <typename T, bool kF32Log, bool kPair>
-const void *fast_kernel_sd(const KParams &kp) {
-  if (kp.source == 1) return reinterpret_cast<const void *>(&batch_kernel_fast<T, kF32Log, kPair, false, true>);
-  return kp.sd_same ? reinterpret_cast<const void *>(&batch_kernel_fast<T, kF32Log, kPair, false, false>)
-                    : reinterpret_cast<const void *>(&batch_kernel_fast<T, kF32Log, kPair, true, false>);
-}
-template <bool kF32Log>
-const void *fast_kernel_mode(const KParams &kp, int g) {
-  switch (g) {
-    case 0: return fast_kernel_sd<uint16_t, kF32Log, true>(kp);
-    case 1: return fast_kernel_sd<uint8_t, kF32Log, true>(kp);
-    case 2: return fast_kernel_sd<uint16_t, kF32Log, false>(kp);
-    default: return fast_kernel_sd<uint8_t, kF32Log, false>(kp);
-  }
-}
-const void *fast_kernel_of(const KParams &kp, int g) {
-  return kp.f32log ? fast_kernel_mode<true>(kp, g) : fast_kernel_mode<false>(kp, g);
-}
-template <bool kF32Log>
-const void *redo_kernel_src(const KParams &kp) {
-  return kp.source == 1 ? reinterpret_cast<const void *>(&batch_kernel_redo<kF32Log, true>)
-                        : reinterpret_cast<const void *>(&batch_kernel_redo<kF32Log, false>);
-}
-const void *redo_kernel_of(const KParams &kp) {
-  return kp.f32log ? redo_kernel_src<true>(kp) : redo_kernel_src<false>(kp);
-}
-
 }  // namespace
+
+// The narrow class's selectors (the compact and wide classes are in
+// fx_plan_compact.cu and fx_plan_wide.cu).
+const void *plan_fast_kernel_narrow(const KParams &kp, int g) { return fast_kernel_of<kNarrowRm>(kp, g); }
+const void *plan_redo_kernel_narrow(const KParams &kp) { return redo_kernel_of<kNarrowRm>(kp); }
+const void *plan_fast_kernel_compact(const KParams &kp, int g);
+const void *plan_redo_kernel_compact(const KParams &kp);
+const void *plan_fast_kernel_wide(const KParams &kp, int g);
+const void *plan_redo_kernel_wide(const KParams &kp);
+
+const void *plan_fast_kernel(int rm_class, const KParams &kp, int g) {
+  if (rm_class == kCompactRm) return plan_fast_kernel_compact(kp, g);
+  if (rm_class == kWideRm) return plan_fast_kernel_wide(kp, g);
+  return plan_fast_kernel_narrow(kp, g);
+}
+const void *plan_redo_kernel(int rm_class, const KParams &kp) {
+  if (rm_class == kCompactRm) return plan_redo_kernel_compact(kp);
+  if (rm_class == kWideRm) return plan_redo_kernel_wide(kp);
+  return plan_redo_kernel_narrow(kp);
+}
+
 }  // namespace fx
 
 using namespace fx;
@@ -198,6 +80,7 @@ struct fx_plan {
   KParams kp8, kp16;
   fx_status st16;  // FX_ERR_RANGE when 16-bit images cannot be evaluated exactly
   bool fast;
+  int rm_class;  // strip class of the streaming path (kCompactRm, kNarrowRm or kWideRm)
   int device, max_images, num_sms;
   // batch workspace, double-buffered: graph i copies host table i into device
   // table i and runs on queue counters i, so two replays (e.g. from two
@@ -257,7 +140,7 @@ size_t unit_smem(const fx_plan *p) {
 // a fixed size so the graph never changes.
 fx_status build_graph(fx_plan *p, int i) {
   p->smem = unit_smem(p);
-  const void *fn = p->fast ? fast_kernel_of(p->kp8, 0) : reinterpret_cast<const void *>(&batch_kernel_general);
+  const void *fn = p->fast ? plan_fast_kernel(p->rm_class, p->kp8, 0) : reinterpret_cast<const void *>(&batch_kernel_general);
   if (!p->fast &&  // the streaming kernels use static shared memory only
       cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) != cudaSuccess)
     return FX_ERR_CUDA;
@@ -300,13 +183,13 @@ fx_status build_graph(fx_plan *p, int i) {
       KParams *kg = gi % 2 == 1 ? &k8 : &k16;  // groups 1 and 3 hold the uint8 images
       void *gargs[] = {&tab, &ctr, &stp, kg};
       cudaKernelNodeParams kf = kn;
-      kf.func = const_cast<void *>(fast_kernel_of(p->kp8, gi));
+      kf.func = const_cast<void *>(plan_fast_kernel(p->rm_class, p->kp8, gi));
       kf.kernelParams = gargs;
       e = cudaGraphAddKernelNode(&n_grp[gi], g, &n_zero, 1, &kf);
     }
     // the integer (or wide) redo pass after all groups, one wave of CTAs
     cudaKernelNodeParams kr = kn;
-    kr.func = const_cast<void *>(redo_kernel_of(p->kp8));
+    kr.func = const_cast<void *>(plan_redo_kernel(p->rm_class, p->kp8));
     kr.sharedMemBytes = 0;
     int occ = 0;
     if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kr.func, 32 * kWarpsPerCta, 0);
@@ -330,7 +213,7 @@ fx_status rebuild(fx_plan *p) {
 fx_status fill_table(fx_plan *p, unsigned char *h, const fx_image_desc *d, int32_t n) {
   BatchHeader *hdr = reinterpret_cast<BatchHeader *>(h);
   BatchImage *ims = reinterpret_cast<BatchImage *>(h + sizeof(BatchHeader));
-  const int uwx = p->fast ? strip_width(p->kp8.source == 1, kNarrowRm) : gen::TW;  // output columns per unit
+  const int uwx = p->fast ? strip_width(p->kp8.source == 1, p->rm_class) : gen::TW;  // output columns per unit
   int uh = p->fast ? p->unit_h : gen::TH;
   if (p->fast && p->auto_h) {
     // the wave model of fx_extract over the whole batch: a warp walks uh rows
@@ -437,10 +320,12 @@ fx_status fx_plan_create(fx_plan **out, const fx_params *params, int32_t max_ima
   }
   p->st16 = make_kparams(params, 65535, &p->kp16);
   if (p->st16 != FX_OK) p->kp16 = p->kp8;
-  p->fast = stream_narrow(p->kp8) && stream_narrow(p->kp16);
+  // the streaming path for median radii up to 7 (both parameter sets share the list)
+  p->fast = fast_path_supported(p->kp8) && fast_path_supported(p->kp16);
+  p->rm_class = strip_class(p->kp8);
   p->device = device;
   p->max_images = max_images;
-  p->unit_w = strip_width(p->kp8.source == 1, kNarrowRm);
+  p->unit_w = strip_width(p->kp8.source == 1, p->rm_class);
   p->unit_h = kDefaultUnitH;
   p->ctas_per_sm = p->fast ? kFirstPassCtas : 2;
   p->auto_h = true;
@@ -524,7 +409,9 @@ fx_status fx_plan_set_tile(fx_plan *p, int32_t tile_w, int32_t tile_h, int32_t c
   if (!p || ctas_per_sm < 1 || ctas_per_sm > 8) return FX_ERR_INVALID_ARG;
   // tile_h 0: the height is picked per batch (the wave model in fill_table)
   const bool automatic = tile_h == 0;
-  if (!fast_unit_shape_ok(tile_w, automatic ? kDefaultUnitH : tile_h, p->kp8.source == 1)) return FX_ERR_INVALID_ARG;
+  const int th = automatic ? kDefaultUnitH : tile_h;
+  if (tile_w != strip_width(p->kp8.source == 1, p->rm_class) || th < 16 || th > 8192 || th % 16 != 0)
+    return FX_ERR_INVALID_ARG;
   DeviceScope dev(p->device);
   if (!dev.ok) return FX_ERR_CUDA;
   for (int i = 0; i < 2; ++i)
@@ -550,12 +437,12 @@ fx_status fx_plan_autotune(fx_plan *p, const fx_image_desc *descs, int32_t n, vo
   fx_status st = FX_OK;
   // candidates: the automatic height (0), then the fixed heights
   for (int c = -1; c < kNumUnitHeights && st == FX_OK; ++c) {
-    const int uw = strip_width(p->kp8.source == 1, kNarrowRm), uh = c < 0 ? 0 : kUnitHeights[c];
+    const int uw = strip_width(p->kp8.source == 1, p->rm_class), uh = c < 0 ? 0 : kUnitHeights[c];
     for (int cps = 1; cps <= kMaxCtasPerSm && st == FX_OK; ++cps) {
       if (!p->fast && uh != 0) continue;
       if ((st = fx_plan_set_tile(p, uw, uh, cps)) != FX_OK) break;
       int occ = 0;
-      if (p->fast) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fast_kernel_of(p->kp8, 0), 32 * kWarpsPerCta, 0);
+      if (p->fast) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, plan_fast_kernel(p->rm_class, p->kp8, 0), 32 * kWarpsPerCta, 0);
       else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batch_kernel_general, 256, p->smem);
       if (occ < cps) continue;
       float t_best = 1e30f;

@@ -340,11 +340,14 @@ def test_batch_matches_single_and_oracle(cuda_lib):
         assert_same(singles[i], oracle.extract(np.ascontiguousarray(batch[i][0]), d8), f"oracle image {i}")
 
 
-def test_batch_full_range_16bit_all_groups(cuda_lib):
+@pytest.mark.parametrize("hmf,uw", [((5,), 52), ((3,), 56), ((7, 5, 3), 44), ((5, 5), 44), ((), 56)])
+def test_batch_full_range_16bit_all_groups(cuda_lib, hmf, uw):
     """All four queue groups (uint16 / uint8, aligned pairs / pixel by pixel)
     in one batch, the uint16 images spanning the full 16-bit range: their
     strips are recomputed by the batched integer redo kernel (one resident
-    wave striding over the units).  Against single-image calls and the oracle."""
+    wave striding over the units).  Each median list on its strip class
+    (narrow 52, compact 56, wide 44 columns), with fixed unit shapes too.
+    Against single-image calls and the oracle."""
     rng = np.random.default_rng(41)
     shapes = [(300, 420, 16), (257, 333, 16), (140, 1000, 8), (211, 97, 8), (90, 64, 16), (77, 53, 8)]
     imgs = []
@@ -354,11 +357,13 @@ def test_batch_full_range_16bit_all_groups(cuda_lib):
         if bits == 16:  # push part of the image towards the top of the range
             base[: h // 2] = np.minimum(base[: h // 2].astype(np.int64) + 40000, 65535).astype(np.uint16)
         imgs.append(base)
-    d, p = pair(4.0)  # features on every image: about 4 % of the uint8 pixels, 30 % of the uint16 ones
+    d, p = pair(4.0, hmf=hmf)  # features on every image: about 4 % of the uint8 pixels, 30 % of the uint16 ones
     pairs = [(dev(i), torch.full(i.shape, 9, dtype=torch.uint8, device="cuda")) for i in imgs]
     singles = [run(cuda_lib, img, p) for img, _ in pairs]
     with cuda_lib.Plan(p, max_images=8) as plan:
-        for shape in [None, (52, 0, 3), (52, 64, 1)]:
+        with pytest.raises(RuntimeError):
+            plan.set_tile(uw + 4, 0, 3)  # another class's width
+        for shape in [None, (uw, 0, 3), (uw, 64, 1)]:
             if shape:
                 plan.set_tile(*shape)
             for o in pairs:
