@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-vs-plain comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-fp32", action="store_true", help="skip the FP32-LoG mode measurement")
+    ap.add_argument("--no-specialize", action="store_true",
+                    help="time the precompiled first pass only (no fx_specialize)")
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the parameter variants (crossing-map source, median levels, grayscale median)")
     ap.add_argument("--side", type=int, default=SIDE, help="band side (default 16384)")
@@ -148,7 +150,7 @@ class ClockSampler:
 
 # ------------------------------------------------------------- profiles
 
-KERNEL_SOURCES = ("fx_internal.h", "fx_stream.cuh", "fx_stream_kernels.cuh", "fx_stream.cu")
+KERNEL_SOURCES = ("fx_internal.h", "fx_checked.cuh", "fx_stream.cuh", "fx_stream_kernels.cuh", "fx_stream.cu", "fx_jit.cpp")
 
 
 def kernel_source_sha() -> str:
@@ -244,6 +246,24 @@ def aggregate_gpx_s(px_per_step_per_rank: int, steps: int, elapsed_ms: float, wo
 
 # ------------------------------------------------------------------ main
 
+def time_band(torch, stream, call, px, warmup=3, reps=10):
+    """Median event-timed duration of call() (one band) on stream."""
+    for _ in range(warmup):
+        call()
+    torch.cuda.synchronize()
+    ms = []
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        call()
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(b))
+    ms.sort()
+    m = ms[len(ms) // 2]
+    return {"ms_per_band": round(m, 4), "gpx_s": round(px / m / 1e6, 1)}
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -284,6 +304,25 @@ def main():
     def barrier():
         if world > 1:
             dist.barrier()
+
+    # ---- the precompiled first pass, timed on band 0 before the specialisation
+    generic = None
+    if not args.no_specialize:
+        generic = time_band(torch, stream, lambda: fx.extract(bands[0], params, out=outs[0], stream=stream),
+                            bands[0].numel())
+    # the first pass compiled at run time with these parameters' masks and
+    # contrast thresholds as constants (fx_specialize, cached per process);
+    # its masks are the precompiled kernel's
+    specialized = False
+    if not args.no_specialize:
+        t0 = time.perf_counter()
+        specialized = fx.specialize(params, fx.FX_U16)
+        if generic is not None:
+            generic["specialize_s"] = round(time.perf_counter() - t0, 2)
+            ref0 = outs[0].clone()
+            fx.extract(bands[0], params, out=outs[0], stream=stream)
+            torch.cuda.synchronize()
+            generic["identical_masks"] = bool(torch.equal(ref0, outs[0]))
 
     for _ in range(max(3, args.warmup)):
         step()
@@ -391,12 +430,13 @@ def main():
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "side": args.side, "bands": BANDS, "values": "12-bit",
                        "launch": "fx_extract per band (streaming kernel + integer redo check)",
+                       "specialized": specialized,
                        "parallelism": f"replicas x{world}", "l2": "inputs larger than L2 (512 MiB per band)"},
             "roofline": roof, "issue_roof": issue, "cpu_baseline": cpu, "e2e": e2e,
             # per band: the streaming kernel and the integer redo check (12-bit data
             # is within the FP32-exact bound, so the redo kernel only reads markers)
             "gpu_launches": K * BANDS * 2, "clocks": clk, "batched": batched, "serving": serving,
-            "fp32_log": fp32, "variants": variants,
+            "fp32_log": fp32, "variants": variants, "precompiled_kernel": generic,
         }
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -41,8 +41,10 @@
 #ifndef FX_H
 #define FX_H
 
+#ifndef __CUDACC_RTC__ /* kernels compiled at run time bring their own fixed-width types */
 #include <stddef.h>
 #include <stdint.h>
+#endif
 
 #ifdef __cplusplus
 extern "C" {
@@ -304,6 +306,23 @@ fx_status fx_hybrid_median(const void *img, int64_t width, int64_t height, int64
 #define FX_NOALLOC_MAX_IMAGES 128
 fx_status fx_extract_batch_noalloc(const fx_params *params, const fx_image_desc *descs, int32_t n,
                                    void *stream);
+
+/*
+ * Compiles, at run time on the current device, fx_extract's streaming first
+ * pass for this parameter set and dtype with the two LoG masks' ring weights
+ * and the contrast thresholds as compile-time constants (NVRTC; a second or
+ * two per call, cached for the life of the process).  Afterwards fx_extract
+ * and the host-buffer entry points use that kernel whenever their parameters
+ * match and the image is read as aligned words (base and pitch multiples of
+ * 4 bytes); other calls use the library's precompiled kernels.  The masks are
+ * identical either way (the same operations, in the same order).  A tuning
+ * aid of this library; the paper has no counterpart.
+ * Errors: FX_ERR_INVALID_ARG, FX_ERR_RANGE; FX_ERR_UNSUPPORTED when the
+ * parameters do not run on the streaming kernel, the library is the checked
+ * build, or run-time compilation is unavailable or fails (then nothing
+ * changes); FX_ERR_CUDA.
+ */
+fx_status fx_specialize(const fx_params *params, fx_dtype dtype);
 
 /*
  * Range-check failures counted by the kernels of the checked build

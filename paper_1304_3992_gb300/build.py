@@ -57,8 +57,13 @@ def _compile(src: str, extra: list[str], build_dir: str = BUILD) -> str:
                "-Xcompiler", "-ffp-contract=off", "--expt-relaxed-constexpr", *inc, *extra,
                "-c", src, "-o", obj]
     else:
+        # the run-time compiler (fx_jit.cpp) reads the kernel headers from the
+        # source tree and the toolkit's libnvrtc
+        paths = [f'-DFX_SRC_DIR="{CSRC}"', f'-DFX_INC_DIR="{os.path.join(ROOT, "include")}"',
+                 f'-DFX_CUDA_LIB_DIR="{os.path.join(_cuda_home(), "lib64")}"']
+        extra = extra + [f"-D{k}={os.environ[k]}" for k in ("FX_FIRST_PASS_CTAS", "FX_WARPS_PER_CTA") if os.environ.get(k)]
         cmd = ["g++", "-O2", "-std=c++17", "-fPIC", "-ffp-contract=off", "-fno-fast-math",
-               "-I" + os.path.join(_cuda_home(), "include"), *inc, *extra, "-c", src, "-o", obj]
+               "-I" + os.path.join(_cuda_home(), "include"), *inc, *paths, *extra, "-c", src, "-o", obj]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"compile failed: {' '.join(cmd)}\n{r.stdout}\n{r.stderr}")
@@ -77,7 +82,7 @@ def build(force: bool = False, verbose: bool = False, extra: list[str] | None = 
     with cf.ThreadPoolExecutor(max_workers=max(1, min(len(srcs), os.cpu_count() or 4))) as ex:
         objs = list(ex.map(lambda s: _compile(s, extra, build_dir), srcs))
     tmp = lib + f".{os.getpid()}.tmp"
-    cmd = ["nvcc", ARCH, "-shared", "-cudart", "static", "-o", tmp, *objs]
+    cmd = ["nvcc", ARCH, "-shared", "-cudart", "static", "-o", tmp, *objs, "-ldl"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed: {' '.join(cmd)}\n{r.stdout}\n{r.stderr}")

@@ -11,7 +11,9 @@
 // In the normal build FX_GUARD(ok) is the constant true and ok is not
 // evaluated.
 #pragma once
+#ifndef __CUDACC_RTC__
 #include <cuda_runtime.h>
+#endif
 
 namespace fx {
 

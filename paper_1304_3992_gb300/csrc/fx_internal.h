@@ -1,9 +1,13 @@
 // fx_internal.h -- types shared by the host side of libfx and its kernels.
+// Kernels compiled at run time (fx_jit.cpp) see the types only: the host
+// declarations are left out under __CUDACC_RTC__.
 #pragma once
 
+#ifndef __CUDACC_RTC__
 #include <cstdint>
 #include <cuda_runtime.h>
 #include <nvtx3/nvToolsExt.h>
+#endif
 
 #include "../../include/fx.h"
 
@@ -59,6 +63,7 @@ struct KParams {
   uint32_t zsel[2][28];
 };
 
+#ifndef __CUDACC_RTC__
 // NVTX range over a host-side scope (launches, copies, pipeline stages); the
 // ranges cost nothing unless a profiler is attached.
 struct NvtxRange {
@@ -67,6 +72,7 @@ struct NvtxRange {
   NvtxRange(const NvtxRange &) = delete;
   NvtxRange &operator=(const NvtxRange &) = delete;
 };
+#endif
 
 // Derive KParams from fx_params for images whose values are <= maxval.
 fx_status make_kparams(const fx_params *p, int32_t maxval, KParams *kp);
@@ -89,6 +95,7 @@ struct ImageView {
   int64_t row_lim;               // rows [row0, row_lim) are present in the buffer
 };
 
+#ifndef __CUDACC_RTC__
 cudaError_t launch_tile_general(const ImageView &v, const KParams &kp, cudaStream_t s);
 
 // Range-check failures counted by the kernels of each translation unit (the
@@ -112,5 +119,10 @@ bool pair_loads_ok(const ImageView &v);
 bool pair_loads_ok(const void *img, int64_t width, int64_t pitch, int64_t elem);
 cudaError_t launch_fast(const ImageView &v, const KParams &kp, cudaStream_t s);
 cudaError_t launch_extract(const ImageView &v, const KParams &kp, cudaStream_t s);
+// The first-pass kernel compiled at run time for kp's masks and contrast
+// thresholds (fx_specialize) for this pixel size, load path and strip class on
+// the current device, or nullptr (fx_jit.cpp).
+const void *specialized_kernel(const KParams &kp, int elem, bool pair, int rm_class);
+#endif
 
 }  // namespace fx

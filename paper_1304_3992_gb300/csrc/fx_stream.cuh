@@ -42,7 +42,9 @@
 // every binary stage at rows / columns outside the image are replaced by
 // those of the nearest image row / column.
 #pragma once
+#ifndef __CUDACC_RTC__
 #include <cstdint>
+#endif
 
 #include "fx_checked.cuh"
 #include "fx_internal.h"
@@ -72,6 +74,17 @@ constexpr int kWarpsPerCta = FX_WARPS_PER_CTA;
 #define FX_FIRST_PASS_CTAS 3
 #endif
 constexpr int kFirstPassCtas = FX_FIRST_PASS_CTAS;
+
+// Where the first pass takes the LoG ring weights and the contrast threshold
+// from: the kernel parameters (RuntimeConsts), or, in a kernel compiled at run
+// time for one parameter set (fx_specialize), compile-time constants that
+// become instruction immediates (a packed FP32x2 operand from the parameters
+// needs a register pair holding the value twice).
+struct RuntimeConsts {
+  static constexpr bool kStatic = false;
+  static __device__ __forceinline__ float w(int, int) { return 0.0f; }
+  static __device__ __forceinline__ float ntzc(int) { return 0.0f; }
+};
 
 inline bool fast_unit_shape_ok(int w, int h, bool src_z) {
   return w == strip_width(src_z, kNarrowRm) && h >= 16 && h <= 8192 && h % 16 == 0;
@@ -193,9 +206,12 @@ struct Ar<kModeF32> {
     return d;
   }
   // sign bits set  <=>  max - min <= t_zc  (contrast test fails), both columns
-  static __device__ __forceinline__ P cfail(const KParams &kp, int f, P mx, P mn) {
+  static __device__ __forceinline__ P cfail_c(float ntzc1f, P mx, P mn) {
     const P d = __ffma2_rn(mn, make_float2(-1.0f, -1.0f), mx);  // max - min, rounded once
-    return __fadd2_rn(d, make_float2(kp.ntzc1f[f], kp.ntzc1f[f]));
+    return __fadd2_rn(d, make_float2(ntzc1f, ntzc1f));
+  }
+  static __device__ __forceinline__ P cfail(const KParams &kp, int f, P mx, P mn) {
+    return cfail_c(kp.ntzc1f[f], mx, mn);
   }
   // Sign bits set  <=>  the standard-deviation test fails (reading R4), for
   // both columns (A3, A5: pixel sums; Q3, Q5: sums of the squared biased bits).
@@ -312,7 +328,9 @@ struct Ar<kModeF32LogWide> : Ar<kModeF32> {
 // kRm: the strip class (kCompactRm, kNarrowRm or kWideRm): the halo, and for
 // the wide class the ring prefill one iteration earlier, so that the rows
 // above the unit that the outputs depend on are computed.
-template <typename T, int kMode, bool kPair, bool kSd2, bool kSrcZ, int kRm = kNarrowRm>
+// Cst: RuntimeConsts, or the constants of a run-time compiled kernel (FP32
+// modes only).
+template <typename T, int kMode, bool kPair, bool kSd2, bool kSrcZ, int kRm = kNarrowRm, class Cst = RuntimeConsts>
 struct Strip {
   using A = Ar<kMode>;
   // halo columns left of the strip (even: the pair loads are aligned) and
@@ -457,6 +475,17 @@ struct Strip {
       }
       raw_[s] = raw1_[s] = 0;
     }
+  }
+
+  // LoG ring weight c of mask f, and the contrast test (sign bits set <=>
+  // max - min <= t_zc) of branch f
+  __device__ __forceinline__ V wgt(int f, int c) const {
+    if constexpr (Cst::kStatic) return static_cast<V>(Cst::w(f, c));
+    else return A::w(kp, f, c);
+  }
+  __device__ __forceinline__ P cfail(int f, P mx, P mn) const {
+    if constexpr (Cst::kStatic) return A::cfail_c(Cst::ntzc(f), mx, mn);
+    else return A::cfail(kp, f, mx, mn);
   }
 
   // Row t (relative to Y0) into ring slot S.  Rows outside the image clamp to
@@ -649,20 +678,20 @@ struct Strip {
         const P d4 = A::fma(-4.0f, R0, R4), d5 = A::fma(-8.0f, R0, R5);
         const P d8 = A::fma(-4.0f, R0, R8);
         // starting from +0: a zero product gives +0, so no sum is ever -0
-        P l = A::fma(A::w(kp, f, 1), d1, A::zero());
-        l = A::fma(A::w(kp, f, 2), d2, l);
-        l = A::fma(A::w(kp, f, 3), d4, l);
-        l = A::fma(A::w(kp, f, 4), d5, l);
-        L_[f][c0] = A::fma(A::w(kp, f, 5), d8, l);
+        P l = A::fma(wgt(f, 1), d1, A::zero());
+        l = A::fma(wgt(f, 2), d2, l);
+        l = A::fma(wgt(f, 3), d4, l);
+        l = A::fma(wgt(f, 4), d5, l);
+        L_[f][c0] = A::fma(wgt(f, 5), d8, l);
       } else {
         // exact partial sums; starting from +0 no sum is ever -0 (the sign bit
         // of L is the sign of the response)
-        P l = A::fma(A::w(kp, f, 0), R0, A::zero());
-        l = A::fma(A::w(kp, f, 1), R1, l);
-        l = A::fma(A::w(kp, f, 2), R2, l);
-        l = A::fma(A::w(kp, f, 3), R4, l);
-        l = A::fma(A::w(kp, f, 4), R5, l);
-        L_[f][c0] = A::fma(A::w(kp, f, 5), R8, l);
+        P l = A::fma(wgt(f, 0), R0, A::zero());
+        l = A::fma(wgt(f, 1), R1, l);
+        l = A::fma(wgt(f, 2), R2, l);
+        l = A::fma(wgt(f, 3), R4, l);
+        l = A::fma(wgt(f, 4), R5, l);
+        L_[f][c0] = A::fma(wgt(f, 5), R8, l);
       }
     }
     if constexpr (!kSrcZ) {
@@ -711,7 +740,7 @@ struct Strip {
                          A::max3(A::max3(c0v, c1v, Le), A::hi(Ln), A::hi(Ls)));
       const P mn = A::mk(A::min3(A::min3(Lw, c0v, c1v), A::lo(Ln), A::lo(Ls)),
                          A::min3(A::min3(c0v, c1v, Le), A::hi(Ln), A::hi(Ls)));
-      const P cf = A::cfail(kp, f, mx, mn);
+      const P cf = cfail(f, mx, mn);
       // column 1 first: bit 30 - 2r + j for row r, column j
       put(acc_[5 * f + 0], A::bits(c1v));
       put(acc_[5 * f + 0], A::bits(c0v));
@@ -1089,11 +1118,12 @@ __device__ __forceinline__ uint32_t (*warp_words(StripWords &w))[32] { return w[
 // kF32Log selects the FP32-LoG mode (KParams::f32log) at compile time; kSd2 =
 // !KParams::sd_same (kSd2 = true is correct for any thresholds); kSrcZ =
 // (KParams::source == 1); kRm = the strip class.
-template <typename T, bool kF32Log, bool kPair, bool kSd2, bool kSrcZ, bool kTail = true, int kRm = kNarrowRm>
+template <typename T, bool kF32Log, bool kPair, bool kSd2, bool kSrcZ, bool kTail = true, int kRm = kNarrowRm,
+          class Cst = RuntimeConsts>
 __device__ __forceinline__ void fast_unit(const ImageView &v, const KParams &kp, int64_t ux, int64_t uy, int,
                                           int uh, uint32_t (*words)[32]) {
   constexpr int kMode = kF32Log ? st::kModeF32Log : st::kModeF32;
-  using S = st::Strip<T, kMode, kPair, kSd2, kSrcZ, kRm>;
+  using S = st::Strip<T, kMode, kPair, kSd2, kSrcZ, kRm, Cst>;
   static_assert(S::kWords + S::kRingRows == kStripWords, "shared word layout");
   if (kp.fbound < 0) return;
   constexpr int uw = strip_width(kSrcZ, kRm);
@@ -1104,6 +1134,20 @@ __device__ __forceinline__ void fast_unit(const ImageView &v, const KParams &kp,
   if (!s.template run<kTail>() && (threadIdx.x & 31) == 0 &&
       FX_GUARD(uy * uh < v.y_end - v.y_begin && ux * uw < v.width))
     *unit_marker(v, ux, uy, uh, uw) = kRedo;
+}
+
+// The streaming first pass of fx_extract: one unit per warp, units in
+// row-band order (unit = CTA * kWarpsPerCta + warp; ux = unit % units_x).  3
+// CTAs (12 warps) per SM in 168 registers.
+template <typename T, bool kF32Log, bool kPair, bool kSd2, bool kSrcZ, int kRm, class Cst>
+__global__ void __launch_bounds__(32 * kWarpsPerCta, kFirstPassCtas)
+    stream_kernel(const __grid_constant__ ImageView v, const __grid_constant__ KParams kp, int64_t units_x,
+                  int64_t units, int uh) {
+  __shared__ StripWords words;
+  const int64_t unit = static_cast<int64_t>(blockIdx.x) * kWarpsPerCta + (threadIdx.x >> 5);
+  if (unit >= units) return;  // whole warps only
+  fast_unit<T, kF32Log, kPair, kSd2, kSrcZ, true, kRm, Cst>(v, kp, unit % units_x, unit / units_x, 0, uh,
+                                                           warp_words(words));
 }
 
 template <typename T, bool kF32Log, bool kSrcZ, int kRm = kNarrowRm>

@@ -10,29 +10,30 @@
 namespace fx {
 namespace {
 
-// The first pass runs 3 CTAs (12 warps) per SM in 168 registers; the redo
-// pass (64-bit sums) runs 2 per SM, where it needs no spill.
-template <typename T, bool kRedoPass, bool kF32Log, bool kPair, bool kSd2, bool kSrcZ, int kRm>
-__global__ void __launch_bounds__(32 * kWarpsPerCta, kRedoPass ? 2 : kFirstPassCtas) stream_kernel(const __grid_constant__ ImageView v,
-                                                                  const __grid_constant__ KParams kp,
-                                                                  int64_t units_x, int64_t units, int uh) {
+// The redo pass (64-bit sums) runs 2 CTAs per SM, where it needs no spill.
+template <typename T, bool kF32Log, bool kSrcZ, int kRm>
+__global__ void __launch_bounds__(32 * kWarpsPerCta, 2) stream_redo_kernel(const __grid_constant__ ImageView v,
+                                                                            const __grid_constant__ KParams kp,
+                                                                            int64_t units_x, int64_t units, int uh) {
   __shared__ StripWords words;
   const int64_t unit = static_cast<int64_t>(blockIdx.x) * kWarpsPerCta + (threadIdx.x >> 5);
   if (unit >= units) return;  // whole warps only
-  if constexpr (kRedoPass)
-    fast_unit_redo<T, kF32Log, kSrcZ, kRm>(v, kp, unit % units_x, unit / units_x, 0, uh, warp_words(words));
-  else
-    fast_unit<T, kF32Log, kPair, kSd2, kSrcZ, true, kRm>(v, kp, unit % units_x, unit / units_x, 0, uh,
-                                                            warp_words(words));
+  fast_unit_redo<T, kF32Log, kSrcZ, kRm>(v, kp, unit % units_x, unit / units_x, 0, uh, warp_words(words));
 }
 
 template <typename T, bool kF32Log, bool kPair, int kRm>
 void launch_first(const ImageView &v, const KParams &kp, cudaStream_t s, unsigned g, int64_t units_x,
                   int64_t units, int uh) {
   constexpr int nt = 32 * kWarpsPerCta;
-  if (kp.source == 1) stream_kernel<T, false, kF32Log, kPair, false, true, kRm><<<g, nt, 0, s>>>(v, kp, units_x, units, uh);
-  else if (kp.sd_same) stream_kernel<T, false, kF32Log, kPair, false, false, kRm><<<g, nt, 0, s>>>(v, kp, units_x, units, uh);
-  else stream_kernel<T, false, kF32Log, kPair, true, false, kRm><<<g, nt, 0, s>>>(v, kp, units_x, units, uh);
+  // a kernel compiled for this parameter set (fx_specialize), if there is one
+  if (const void *jk = specialized_kernel(kp, sizeof(T), kPair, kRm)) {
+    void *args[] = {const_cast<ImageView *>(&v), const_cast<KParams *>(&kp), &units_x, &units, &uh};
+    if (cudaLaunchKernel(jk, dim3(g), dim3(nt), args, 0, s) == cudaSuccess) return;
+  }
+  using C = RuntimeConsts;
+  if (kp.source == 1) stream_kernel<T, kF32Log, kPair, false, true, kRm, C><<<g, nt, 0, s>>>(v, kp, units_x, units, uh);
+  else if (kp.sd_same) stream_kernel<T, kF32Log, kPair, false, false, kRm, C><<<g, nt, 0, s>>>(v, kp, units_x, units, uh);
+  else stream_kernel<T, kF32Log, kPair, true, false, kRm, C><<<g, nt, 0, s>>>(v, kp, units_x, units, uh);
 }
 
 template <typename T, bool kF32Log, int kRm>
@@ -46,8 +47,8 @@ void launch_mode(const ImageView &v, const KParams &kp, cudaStream_t s, int64_t 
   }
   // the second pass recomputes the strips the first one marked (all when fbound < 0)
   if (kp.fbound < 0 || kp.fbound < (sizeof(T) == 1 ? 255 : 65535)) {
-    if (kp.source == 1) stream_kernel<T, true, kF32Log, false, true, true, kRm><<<g, nt, 0, s>>>(v, kp, units_x, units, uh);
-    else stream_kernel<T, true, kF32Log, false, true, false, kRm><<<g, nt, 0, s>>>(v, kp, units_x, units, uh);
+    if (kp.source == 1) stream_redo_kernel<T, kF32Log, true, kRm><<<g, nt, 0, s>>>(v, kp, units_x, units, uh);
+    else stream_redo_kernel<T, kF32Log, false, kRm><<<g, nt, 0, s>>>(v, kp, units_x, units, uh);
   }
 }
 

@@ -88,6 +88,7 @@ _SIGNATURES = {
                                         ctypes.c_int, ctypes.c_int32, ctypes.c_void_p, ctypes.c_int64,
                                         ctypes.c_void_p]),
     "fx_checked_violations": (ctypes.c_int, [ctypes.POINTER(ctypes.c_uint64), ctypes.c_int32]),
+    "fx_specialize": (ctypes.c_int, [ctypes.POINTER(Params), ctypes.c_int]),
     "fx_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "fx_version": (ctypes.c_char_p, []),
 }
@@ -302,6 +303,18 @@ class Plan:
             arr[i].dtype, arr[i].out_mask, arr[i].out_pitch = dt, out.ctypes.data, out.strides[0]
         _check(self._lib.fx_extract_host_batch(self._h, arr, len(pairs)), "fx_extract_host_batch")
         return [out for _, out in pairs]
+
+
+def specialize(params: "Params", dtype: int) -> bool:
+    """fx_specialize: compile the streaming first pass for these parameters
+    and dtype (FX_U8 / FX_U16) on the current device; False when run-time
+    compilation is unavailable (FX_ERR_UNSUPPORTED), an exception on other
+    errors."""
+    code = load().fx_specialize(ctypes.byref(params), dtype)
+    if code == 2:
+        return False
+    _check(code, "fx_specialize")
+    return True
 
 
 def checked_violations(reset: bool = False):

@@ -1,0 +1,96 @@
+"""fx_specialize: the streaming first pass compiled at run time with one
+parameter set's LoG ring weights and contrast thresholds as constants.  Its
+masks must equal the precompiled kernel's and the oracle's for every strip
+class, load mode and standard-deviation variant it serves."""
+import numpy as np
+import pytest
+import torch
+
+from gen import scenes
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+
+def _extract(fx, img, p):
+    out = torch.empty(img.shape, dtype=torch.uint8, device="cuda")
+    fx.extract(img, p, out=out)
+    torch.cuda.synchronize()
+    return out.cpu().numpy()
+
+
+CASES = [
+    ("default", dict()),
+    ("median 3 (compact strips)", dict(hmf=(3,))),
+    ("no median (compact strips)", dict(hmf=())),
+    ("median 7, 5, 3 (wide strips)", dict(hmf=(7, 5, 3))),
+    ("branch thresholds differ", dict(t_sd5=(5.0, 7.0), t_sd3=(4.0, 6.0), t_sdmax=(20.0, 30.0))),
+    ("crossing-map deviation", dict(stddev_source=1, t_sd5=(0.2, 0.3), t_sdmax=(0.45, 0.5), t_sd3=(0.3, 0.4))),
+    ("other masks", dict(sigma=(0.8, 3.0), t_zc=(900.0, 400.0))),
+]
+
+
+@pytest.mark.parametrize("bits", [12, 8])
+@pytest.mark.parametrize("name,kw", CASES, ids=[c[0] for c in CASES])
+def test_specialized_matches_generic_and_oracle(cuda_lib, name, kw, bits):
+    from paper_1304_3992_gb300 import fx
+    h, w = 700, 1100
+    img = scenes.scene(w, h, seed=bits * 31 + len(name), n_rects=300, noise_sigma=4.0 * (1 << (bits - 8)),
+                       impulse_frac=0.01, bits=bits)
+    scale = float(1 << (bits - 8))
+    dtype = fx.FX_U8 if bits == 8 else fx.FX_U16
+    d = oracle.default_params(scale)
+    d.update(kw)
+    p = fx.params_from_dict(d, dtype)
+    x = torch.from_numpy(img).cuda()
+    generic = _extract(fx, x, p)
+    assert fx.specialize(p, dtype), "run-time compilation unavailable"
+    special = _extract(fx, x, p)
+    assert np.array_equal(special, generic), f"{name}: {int((special != generic).sum())} pixels differ"
+    ref = oracle.extract(img, d)
+    assert np.array_equal(special, ref), f"{name}: {int((special != ref).sum())} pixels differ from the oracle"
+    assert special.sum() > 0
+
+
+def test_specialized_fp32_log_mode(cuda_lib):
+    """The FP32-LoG mode (non-integer masks): specialised and precompiled
+    kernels give the same masks."""
+    from paper_1304_3992_gb300 import fx
+    img = scenes.scene(900, 600, seed=5, n_rects=250, noise_sigma=16.0, impulse_frac=0.01, bits=12)
+    p = fx.make_params(fx.FX_U16, 12, log_mode=fx.FX_LOG_FP32)
+    x = torch.from_numpy(img).cuda()
+    generic = _extract(fx, x, p)
+    assert fx.specialize(p, fx.FX_U16)
+    assert np.array_equal(_extract(fx, x, p), generic)
+
+
+def test_specialized_full_band_seams(cuda_lib):
+    """Band 0 of the benchmark, specialised (the benchmark's configuration):
+    40-row bands across the first three unit seams, the top and bottom rows
+    and one random band, against the oracle; then the whole band against the
+    precompiled kernel's mask through another parameter object with the same
+    values (the cache is keyed by value)."""
+    import fullsize
+    from paper_1304_3992_gb300 import fx
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    uh = fullsize.unit_height(16384, 16384, sms)
+    band = next(iter(scenes.ms_bands_u16_12bit()))
+    d = oracle.default_params(16.0)
+    p = fx.params_from_dict(d, fx.FX_U16)
+    x = torch.from_numpy(band).cuda()
+    assert fx.specialize(p, fx.FX_U16)
+    got = _extract(fx, x, p)
+    for y0, y1 in fullsize.seam_bands(band.shape[0], uh, seed=3):
+        ref = oracle.extract(band, d, rows=(y0, y1))
+        assert np.array_equal(got[y0:y1], ref), f"rows {y0}:{y1}"
+    p2 = fx.params_from_dict(dict(d), fx.FX_U16)
+    assert np.array_equal(_extract(fx, x, p2), got)
+
+
+def test_specialize_rejects_bad_arguments(cuda_lib):
+    from paper_1304_3992_gb300 import fx
+    p = fx.make_params(fx.FX_U16, 12)
+    with pytest.raises(RuntimeError):
+        fx.specialize(p, 7)
+    # lists beyond the streaming kernel's radii (the general kernel) are not specialised
+    assert not fx.specialize(fx.make_params(fx.FX_U16, 12, hmf=(7, 7, 7)), fx.FX_U16)
