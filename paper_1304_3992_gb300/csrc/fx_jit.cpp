@@ -77,7 +77,7 @@ const Nvrtc &nvrtc() {
 
 // The kernel variant and the constants it bakes in.
 struct Variant {
-  int device, elem, pair, rm_class, f32log, sd2, src_z;
+  int device, elem, pair, rm_class, f32log, sd2, src_z, nhmf, hmf[FX_MAX_HMF_LEVELS], check;
   float w[2][6], ntzc[2];
 };
 
@@ -91,6 +91,10 @@ Variant variant_of(int device, const KParams &kp, int elem, bool pair, int rm_cl
   v.f32log = kp.f32log ? 1 : 0;
   v.src_z = kp.source == 1 ? 1 : 0;
   v.sd2 = (!v.src_z && !kp.sd_same) ? 1 : 0;
+  v.nhmf = kp.nhmf;
+  for (int l = 0; l < kp.nhmf && l < FX_MAX_HMF_LEVELS; ++l) v.hmf[l] = kp.hmf[l];
+  // the first pass's bound check (the kernels' A::kChecked holds for every FP32 first pass)
+  v.check = kp.fbound < (elem == 1 ? 255 : 65535) ? 1 : 0;
   std::memcpy(v.w, kp.ringf, sizeof v.w);
   std::memcpy(v.ntzc, kp.ntzc1f, sizeof v.ntzc);
   return v;
@@ -132,7 +136,13 @@ std::string source_of(const Variant &v) {
   }
   s += "};\n    return t[f][c];\n  }\n";
   s += "  static __device__ __forceinline__ float ntzc(int f) { return f ? " + hexf(v.ntzc[1]) + " : " +
-       hexf(v.ntzc[0]) + "; }\n};\n";
+       hexf(v.ntzc[0]) + "; }\n";
+  s += "  static constexpr int kNhmf = " + std::to_string(v.nhmf) + ";\n";
+  s += "  static constexpr bool kCheck = " + std::string(v.check ? "true" : "false") + ";\n";
+  s += "  static __device__ __forceinline__ int hmf(int l) { constexpr int t[" + std::to_string(FX_MAX_HMF_LEVELS) +
+       "] = {";
+  for (int l = 0; l < FX_MAX_HMF_LEVELS; ++l) s += (l ? ", " : "") + std::to_string(v.hmf[l]);
+  s += "}; return t[l]; }\n};\n";
   return s;
 }
 

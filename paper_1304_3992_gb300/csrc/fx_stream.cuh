@@ -80,10 +80,16 @@ constexpr int kFirstPassCtas = FX_FIRST_PASS_CTAS;
 // time for one parameter set (fx_specialize), compile-time constants that
 // become instruction immediates (a packed FP32x2 operand from the parameters
 // needs a register pair holding the value twice).
+// A kernel compiled for one parameter set also fixes the median list (kNhmf
+// levels of windows hmf(l)) and whether loaded values are checked against the
+// FP32-exact bound (kCheck).
 struct RuntimeConsts {
   static constexpr bool kStatic = false;
+  static constexpr int kNhmf = 0;
+  static constexpr bool kCheck = false;
   static __device__ __forceinline__ float w(int, int) { return 0.0f; }
   static __device__ __forceinline__ float ntzc(int) { return 0.0f; }
+  static __device__ __forceinline__ int hmf(int) { return 0; }
 };
 
 inline bool fast_unit_shape_ok(int w, int h, bool src_z) {
@@ -403,7 +409,7 @@ struct Strip {
     W = v.width;
     H = v.height;
     xs = X0 - kLeftHalo;
-    check = A::kChecked && kp.fbound < (sizeof(T) == 1 ? 255 : 65535);
+    check = Cst::kStatic ? Cst::kCheck : A::kChecked && kp.fbound < (sizeof(T) == 1 ? 255 : 65535);
     border = xs < 0 || xs + kWinCols > W;
     vstore = (reinterpret_cast<uintptr_t>(v.out) % 2 == 0) && (v.out_pitch % 2 == 0) && (xs % 2 == 0);
     const int64_t bl = -xs, br = W - 1 - xs;  // window columns of image columns 0 and W-1
@@ -487,6 +493,10 @@ struct Strip {
     if constexpr (Cst::kStatic) return A::cfail_c(Cst::ntzc(f), mx, mn);
     else return A::cfail(kp, f, mx, mn);
   }
+  // the median list and the bound check, fixed or from the parameters
+  __device__ __forceinline__ int nhmf() const { return Cst::kStatic ? Cst::kNhmf : kp.nhmf; }
+  __device__ __forceinline__ int hmf_at(int l) const { return Cst::kStatic ? Cst::hmf(l) : kp.hmf[l]; }
+  __device__ __forceinline__ bool checking() const { return Cst::kStatic ? Cst::kCheck : check; }
 
   // Row t (relative to Y0) into ring slot S.  Rows outside the image clamp to
   // it (reading R2); rows outside the buffer (a row band) clamp to the buffer:
@@ -603,7 +613,7 @@ struct Strip {
       }
       const uint32_t b2 = __byte_perm(r0, 0x4B000000u, selb0_);
       const uint32_t b3 = __byte_perm(kPair ? r0 : r1, 0x4B000000u, selb1_);
-      if (check) track_max(kPair ? r0 : __byte_perm(r0, r1, 0x5410));
+      if (checking()) track_max(kPair ? r0 : __byte_perm(r0, r1, 0x5410));
       if constexpr (!kAsync) load_row<S, kChk>(t + 4);
       const uint32_t b0 = __shfl_up_sync(kFull, b2, 1), b1 = __shfl_up_sync(kFull, b3, 1);
       const uint32_t b4 = __shfl_down_sync(kFull, b2, 1), b5 = __shfl_down_sync(kFull, b3, 1);
@@ -621,7 +631,7 @@ struct Strip {
     } else {
       const uint32_t w = pixels<S>();
       load_row<S, kChk>(t + 4);  // four rows ahead, into the slot just read
-      if (check) track_max(w);
+      if (checking()) track_max(w);
       const uint32_t hl = __shfl_up_sync(kFull, w, 1);    // columns -2, -1
       const uint32_t hr = __shfl_down_sync(kFull, w, 1);  // columns 2, 3
       const uint32_t u[6] = {hl & 0xFFFFu, hl >> 16, w & 0xFFFFu, w >> 16, hr & 0xFFFFu, hr >> 16};
@@ -950,7 +960,7 @@ struct Strip {
 
   // End of the 16 steps of group g: block g is packed in acc_.
   __device__ __forceinline__ bool end_group(int64_t g) {
-    if (check) {
+    if (checking()) {
       if (__any_sync(kFull, tracked_max() > static_cast<uint32_t>(kp.fbound))) return false;
     }
     uint32_t m = 0;
@@ -985,12 +995,12 @@ struct Strip {
     // gm - l - 1 from level l of blocks gm - l - 2 .. gm - l; every level but
     // the last is a replicated stage (reading R2).  Without a median the mask
     // of block gm - 1 is stored (the same one block of delay).
-    const int nl = kp.nhmf;
+    const int nl = nhmf();
     uint32_t cur = m;
     if (kRm <= kCompactRm || nl <= 1) {  // a single level (or none) without the level loop
       const uint32_t a = sw_[kLev][lane];
       // compact strips: the one level is a window-3 median
-      if (gm >= 1) store(gm - 1, nl ? median(sw_[kLev + 1][lane], a, m, kRm <= kCompactRm ? 3 : kp.hmf[0]) : a);
+      if (gm >= 1) store(gm - 1, nl ? median(sw_[kLev + 1][lane], a, m, kRm <= kCompactRm ? 3 : hmf_at(0)) : a);
       sw_[kLev + 1][lane] = a;
       sw_[kLev][lane] = m;
     } else {
@@ -999,7 +1009,7 @@ struct Strip {
         const uint32_t a = sw_[kLev + 2 * l][lane], b = sw_[kLev + 2 * l + 1][lane];
         sw_[kLev + 2 * l + 1][lane] = a;
         sw_[kLev + 2 * l][lane] = cur;
-        const uint32_t h = median(b, a, cur, kp.hmf[l]);
+        const uint32_t h = median(b, a, cur, hmf_at(l));
         if (!FX_GUARD(l < FX_MAX_HMF_LEVELS && kLev + 2 * l + 2 <= kZA)) break;
         cur = l + 1 < nl ? replicate(gm - l - 1, h, sw_[kLev + 2 * l + 2][lane]) : h;
       }
@@ -1047,7 +1057,7 @@ struct Strip {
     const uint32_t ring0 = ring_h_;
     const int32_t bmax = static_cast<int32_t>((Y1 - Y0 + 2) / 16);
     // one more block of delay per extra median level and for the crossing-map source
-    const int32_t iters = 4 * (bmax + 2 + (kp.nhmf > 1 ? kp.nhmf : 1) + (kSrcZ ? 1 : 0));
+    const int32_t iters = 4 * (bmax + 2 + (nhmf() > 1 ? nhmf() : 1) + (kSrcZ ? 1 : 0));
     // the last step whose row feeds an output: the bits of row r are packed at
     // step r + 3, and the last output row needs the median radius, its south
     // neighbour (+1) and, for the crossing-map source, the deviation's 2 rows
