@@ -316,7 +316,8 @@ def main():
     specialized = False
     if not args.no_specialize:
         t0 = time.perf_counter()
-        specialized = fx.specialize(params, fx.FX_U16)
+        # uint16 for the bands, uint8 too for the batched scenes and the server
+        specialized = fx.specialize(params, fx.FX_U16) and fx.specialize(params, fx.FX_U8)
         if generic is not None:
             generic["specialize_s"] = round(time.perf_counter() - t0, 2)
             ref0 = outs[0].clone()

@@ -7,8 +7,10 @@
 // moves and spills.  fx_specialize compiles fx::stream_kernel (fx_stream.cuh)
 // with NVRTC, the weights and thresholds of one parameter set being
 // compile-time constants (instruction immediates), and caches the kernel per
-// device, pixel size, load path, strip class and constants.  fx_extract, and
-// the host-buffer path, launch it whenever their parameters match; the
+// device, pixel size, load path, strip class and constants; it does the same
+// for the batched path's group kernel (fx::batch_kernel_fast).  fx_extract and
+// the host-buffer path launch it whenever their parameters match, and plans
+// created afterwards put it in their graphs; the
 // arithmetic is the same, so the masks are identical either way.  NVRTC is
 // loaded on first use (dlopen); without it fx_specialize reports
 // FX_ERR_UNSUPPORTED and every call runs the precompiled kernels.
@@ -77,13 +79,15 @@ const Nvrtc &nvrtc() {
 
 // The kernel variant and the constants it bakes in.
 struct Variant {
+  int kind;  // 0: fx_extract's first pass (stream_kernel), 1: the batched group kernel (batch_kernel_fast)
   int device, elem, pair, rm_class, f32log, sd2, src_z, nhmf, hmf[FX_MAX_HMF_LEVELS], check;
   float w[2][6], ntzc[2];
 };
 
-Variant variant_of(int device, const KParams &kp, int elem, bool pair, int rm_class) {
+Variant variant_of(int kind, int device, const KParams &kp, int elem, bool pair, int rm_class) {
   Variant v;
   std::memset(&v, 0, sizeof v);
+  v.kind = kind;
   v.device = device;
   v.elem = elem;
   v.pair = pair ? 1 : 0;
@@ -113,7 +117,7 @@ std::string hexf(float x) {
 }
 
 std::string name_of(const Variant &v) {
-  return std::string("fx::stream_kernel<") + (v.elem == 1 ? "unsigned char" : "unsigned short") + ", " +
+  return std::string(v.kind ? "fx::batch_kernel_fast<" : "fx::stream_kernel<") + (v.elem == 1 ? "unsigned char" : "unsigned short") + ", " +
          (v.f32log ? "true" : "false") + ", " + (v.pair ? "true" : "false") + ", " + (v.sd2 ? "true" : "false") +
          ", " + (v.src_z ? "true" : "false") + ", " + std::to_string(v.rm_class) + ", JitConsts>";
 }
@@ -124,7 +128,7 @@ std::string source_of(const Variant &v) {
       "typedef unsigned short uint16_t; typedef int int32_t; typedef unsigned int uint32_t;\n"
       "typedef long long int64_t; typedef unsigned long long uint64_t; typedef unsigned long uintptr_t;\n"
       "typedef unsigned long size_t;\n"
-      "#include \"fx_stream.cuh\"\n"
+      "#include \"fx_stream.cuh\"\n#include \"fx_plan_kernels.cuh\"\n"
       "struct JitConsts {\n"
       "  static constexpr bool kStatic = true;\n"
       "  static __device__ __forceinline__ float w(int f, int c) {\n"
@@ -192,35 +196,47 @@ const void *build(const Variant &v) {
 
 }  // namespace
 
-const void *specialized_kernel(const KParams &kp, int elem, bool pair, int rm_class) {
+namespace {
+const void *lookup(int kind, const KParams &kp, int elem, bool pair, int rm_class) {
   if (__atomic_load_n(&g_entries, __ATOMIC_ACQUIRE) == 0) return nullptr;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
-  const std::string key = key_of(variant_of(dev, kp, elem, pair, rm_class));
+  const std::string key = key_of(variant_of(kind, dev, kp, elem, pair, rm_class));
   std::lock_guard<std::mutex> lock(g_mu);
   const auto it = g_cache.find(key);
   return it == g_cache.end() ? nullptr : it->second;
 }
+}  // namespace
 
-// Compiles the pair-load first pass for kp (the load path of images whose base
-// and pitch are multiples of 4 bytes) on the current device.
+const void *specialized_kernel(const KParams &kp, int elem, bool pair, int rm_class) {
+  return lookup(0, kp, elem, pair, rm_class);
+}
+const void *specialized_batch_kernel(const KParams &kp, int elem, int rm_class) {
+  return lookup(1, kp, elem, true, rm_class);
+}
+
+// Compiles the pair-load first pass of fx_extract and of the batched path for
+// kp (the load path of images whose base and pitch are multiples of 4 bytes)
+// on the current device.
 fx_status specialize(const KParams &kp, int elem) {
   if (checked_build()) return FX_ERR_UNSUPPORTED;  // its kernels count range-check failures
   if (kp.fbound < 0 || !fast_path_supported(kp)) return FX_ERR_UNSUPPORTED;
   if (!nvrtc().ok) return FX_ERR_UNSUPPORTED;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return FX_ERR_CUDA;
-  const Variant v = variant_of(dev, kp, elem, true, strip_class(kp));
-  const std::string key = key_of(v);
-  {
+  for (int kind = 0; kind < 2; ++kind) {
+    const Variant v = variant_of(kind, dev, kp, elem, true, strip_class(kp));
+    const std::string key = key_of(v);
+    {
+      std::lock_guard<std::mutex> lock(g_mu);
+      if (g_cache.count(key)) continue;
+    }
+    const void *k = build(v);
+    if (!k) return FX_ERR_UNSUPPORTED;
     std::lock_guard<std::mutex> lock(g_mu);
-    if (g_cache.count(key)) return FX_OK;
+    g_cache[key] = k;
+    __atomic_store_n(&g_entries, static_cast<int>(g_cache.size()), __ATOMIC_RELEASE);
   }
-  const void *k = build(v);
-  if (!k) return FX_ERR_UNSUPPORTED;
-  std::lock_guard<std::mutex> lock(g_mu);
-  g_cache[key] = k;
-  __atomic_store_n(&g_entries, static_cast<int>(g_cache.size()), __ATOMIC_RELEASE);
   return FX_OK;
 }
 

@@ -4,7 +4,9 @@
 // compile in parallel; the kernels have internal linkage and each class
 // exports its kernel selectors (fx_plan_kernels_of).
 #pragma once
+#ifndef __CUDACC_RTC__
 #include <cstdint>
+#endif
 
 #include "fx_internal.h"
 #include "fx_stream.cuh"
@@ -60,18 +62,22 @@ __device__ inline ImageView view_of(const BatchImage &b) {
   return ImageView{b.img, b.width, b.height, b.pitch, 0, b.elem, b.out, b.out_pitch, 0, b.height, b.height};
 }
 
+#ifndef __CUDACC_RTC__
 // The streaming kernels of the batched path for one strip class: group g's
 // first pass and the redo pass, for a plan's parameters.
 const void *plan_fast_kernel(int rm_class, const KParams &kp, int g);
 const void *plan_redo_kernel(int rm_class, const KParams &kp);
-
-namespace {
+// group kernel compiled at run time for kp (fx_specialize), or nullptr (fx_jit.cpp)
+const void *specialized_batch_kernel(const KParams &kp, int elem, int rm_class);
+#endif
 
 // One group of the streaming path (load path kPair, pixel type T): its units
 // from counter[g].  Each group is a kernel of its own, so a kernel holds one
 // strip loop (the register allocation and instruction working set of the
 // single-image kernel).
-template <typename T, bool kF32Log, bool kPair, bool kSd2, bool kSrcZ, int kRm>
+// Cst: as for fx_extract's first pass (RuntimeConsts, or the constants of a
+// kernel compiled at run time for one parameter set).
+template <typename T, bool kF32Log, bool kPair, bool kSd2, bool kSrcZ, int kRm, class Cst = RuntimeConsts>
 __global__ void __launch_bounds__(32 * kWarpsPerCta, kFirstPassCtas) batch_kernel_fast(const unsigned char *table,
                                                                       unsigned long long *counter, int *status,
                                                                       const __grid_constant__ KParams kp) {
@@ -95,9 +101,13 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta, kFirstPassCtas) batch_kerne
     const ImageView v = view_of(b);
     const long long local = u - b.unit_begin;
     const int64_t ux = local % b.units_x, uy = local / b.units_x;
-    fast_unit<T, kF32Log, kPair, kSd2, kSrcZ, false, kRm>(v, kp, ux, uy, hdr->unit_w, hdr->unit_h, warp_words(words));
+    fast_unit<T, kF32Log, kPair, kSd2, kSrcZ, false, kRm, Cst>(v, kp, ux, uy, hdr->unit_w, hdr->unit_h,
+                                                              warp_words(words));
   }
 }
+
+#ifndef __CUDACC_RTC__
+namespace {
 
 // Second pass of the streaming path: every warp walks the units with a static
 // stride and recomputes, on the integer (or wide FP32-LoG) path, the strips
@@ -161,4 +171,5 @@ const void *redo_kernel_of(const KParams &kp) {
 }
 
 }  // namespace
+#endif
 }  // namespace fx

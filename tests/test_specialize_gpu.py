@@ -94,3 +94,39 @@ def test_specialize_rejects_bad_arguments(cuda_lib):
         fx.specialize(p, 7)
     # lists beyond the streaming kernel's radii (the general kernel) are not specialised
     assert not fx.specialize(fx.make_params(fx.FX_U16, 12, hmf=(7, 7, 7)), fx.FX_U16)
+
+
+@pytest.mark.parametrize("hmf", [(5,), (3,), (7, 5, 3)])
+def test_specialized_batched_path(cuda_lib, hmf):
+    """Plans created after fx_specialize put the compiled group kernels (the
+    aligned-load groups) in their graphs: uneven uint8 / uint16 scenes with
+    256-byte pitches, batched, against single calls of the precompiled
+    kernels and, on sampled bands, the oracle."""
+    from paper_1304_3992_gb300 import fx
+    batch = scenes.uneven_batch(n=6, lo=200, hi=1300, seed=21, master_side=1400)
+    d = oracle.default_params(16.0)
+    d["hmf"] = hmf
+    p = fx.params_from_dict(d, fx.FX_U16)
+    imgs = []
+    for v, _ in batch:
+        h, w = v.shape
+        pitch = (w * v.itemsize + 255) // 256 * 256
+        buf = torch.zeros((h, pitch // v.itemsize), dtype=torch.uint8 if v.itemsize == 1 else torch.uint16,
+                          device="cuda")
+        buf[:, :w] = torch.from_numpy(np.ascontiguousarray(v)).cuda()
+        imgs.append(buf[:, :w])
+    singles = [_extract(fx, x, p) for x in imgs]  # before any specialisation of these parameters
+    assert fx.specialize(p, fx.FX_U16) and fx.specialize(p, fx.FX_U8)
+    outs = [torch.full(x.shape, 9, dtype=torch.uint8, device="cuda") for x in imgs]
+    with fx.Plan(p, max_images=8) as plan:
+        plan.extract_batch(list(zip(imgs, outs)))
+        torch.cuda.synchronize()
+        assert plan.device_status() == 0
+    for i, (o, single) in enumerate(zip(outs, singles)):
+        assert np.array_equal(o.cpu().numpy(), single), f"scene {i}"
+    d8 = oracle.default_params(16.0)
+    d8["hmf"] = hmf
+    for i in (0, 1):
+        view = np.ascontiguousarray(batch[i][0])
+        ref = oracle.extract(view, d8, rows=(0, min(64, view.shape[0])))
+        assert np.array_equal(singles[i][:ref.shape[0]], ref), f"oracle scene {i}"
