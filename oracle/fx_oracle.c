@@ -160,7 +160,8 @@ typedef struct {
 
 static int plane_init(plane *p, long long W, long long H, long long y_lo, long long y_hi) {
   p->W = W; p->H = H; p->y_lo = y_lo; p->y_hi = y_hi; p->bad = 0;
-  p->v = (double *)calloc((size_t)((y_hi - y_lo) * W), sizeof(double));
+  const long long n = (y_hi > y_lo ? y_hi - y_lo : 0) * (W > 0 ? W : 0);
+  p->v = (double *)calloc(n > 0 ? (size_t)n : 1, sizeof(double));
   return p->v ? O_OK : O_NOMEM;
 }
 
