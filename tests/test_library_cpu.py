@@ -84,6 +84,23 @@ def test_invalid_arguments_rejected_before_any_device_call(fx):
     assert lib.fx_extract(4096, 8, 8, 16, fx.FX_U16, ctypes.byref(q), 1 << 20, None) == 1
 
 
+def test_specialize_argument_checks(fx):
+    """fx_specialize validates before touching a device or the run-time
+    compiler: null parameters, a wrong struct size or dtype are rejected,
+    parameters that overflow the exact evaluation return FX_ERR_RANGE, and
+    median lists beyond the streaming kernel are not specialised."""
+    lib = fx.load()
+    p = fx.make_params(fx.FX_U16, 12)
+    assert lib.fx_specialize(None, fx.FX_U16) == 1
+    assert lib.fx_specialize(ctypes.byref(p), 3) == 1
+    q = fx.make_params(fx.FX_U16, 12)
+    q.struct_size = 7
+    assert lib.fx_specialize(ctypes.byref(q), fx.FX_U16) == 1
+    big = fx.make_params(fx.FX_U16, 16, mask_q=1 << 19)
+    assert lib.fx_specialize(ctypes.byref(big), fx.FX_U16) == 3
+    assert lib.fx_specialize(ctypes.byref(fx.make_params(fx.FX_U16, 12, hmf=(7, 7, 7))), fx.FX_U16) == 2
+
+
 def test_plan_argument_checks(fx):
     lib = fx.load()
     h = ctypes.c_void_p()
