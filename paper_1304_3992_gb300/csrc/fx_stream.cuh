@@ -377,12 +377,19 @@ struct Strip {
   uint32_t (*sw_)[32];
   static constexpr int kBlk = 0, kPneg = 12, kPpos = 14, kPsS = 16, kLev = 18, kMA = kLev, kZA = 26, kZB = 28,
                        kPcf = 30, kWords = 32;
-  // kAsync (pixel pairs on the FP32 paths): the input rows arrive in an 8-row
-  // ring of words in shared memory (kRing .. kRing + 7), filled by cp.async
-  // seven rows ahead, so loads in flight hold no registers.  A lane's word is
+  // kAsync (the FP32 paths): the input rows arrive in an 8-row ring of words
+  // in shared memory (kRing .. kRing + 7), filled by cp.async seven rows
+  // ahead, so loads in flight hold no registers.  With kPair a lane's word is
   // its uint16 pair, or for uint8 the aligned 4-byte word holding its pair.
-  static constexpr bool kAsync = kPair && A::kBiased;
-  static constexpr int kRing = kWords, kRingRows = 8;
+  // Without (kTwoWord: base or pitch not a multiple of 4 bytes) a lane copies
+  // the aligned 4-byte word holding its first pixel and, when its pixels run
+  // past that word, the next one into a second ring (kRing2 .. kRing2 + 7);
+  // the row's byte offset selects the pixels (each word holds an image byte,
+  // so it lies in that byte's page).
+  static constexpr bool kAsync = A::kBiased;
+  static constexpr bool kTwoWord = kAsync && !kPair;
+  static constexpr int kRing = kWords, kRingRows = 8, kRing2 = kWords + kRingRows;
+  static constexpr uint32_t kRing2Off = 128u * kRingRows;  // bytes from a ring word to its second-ring word
   __device__ __forceinline__ uint32_t &blk(int i) { return sw_[kBlk + i][lane]; }
 
   // load state: rows relative to Y0; p0_ / p1_ address row rbase
@@ -401,6 +408,8 @@ struct Strip {
   // W - 1 of an odd-width row with pitch slack)
   uint32_t ring_base_;
   bool colok_;
+  // kTwoWord: pixel-selector base (byte offset 0) and bytes the lane's pixels span
+  uint32_t psel_c_, span_;
 
   __device__ Strip(const ImageView &v_, const KParams &kp_, int64_t x0, int64_t y0, int64_t y1,
                    uint32_t (*words)[32])
@@ -465,6 +474,18 @@ struct Strip {
       colok_ = d0 >= 0 && d0 < W && d1 >= 0 && d1 < W;
       sel_ = 0x5410u;
       selb0_ = selb1_ = 0x7410u;  // each load holds one zero-extended pixel
+      if constexpr (kTwoWord) {
+        // the pixels as a pair word: bytes (o, o + 1, o + 2 dl, o + 2 dl + 1) of
+        // the two words for uint16, (o, o + dl, o, o) for uint8, o being the
+        // row's byte offset in the first word and dl = d1 - d0 (0 at a border)
+        const uint32_t dl = static_cast<uint32_t>(d1 - d0);
+        psel_c_ = sizeof(T) == 2 ? (0x0010u | ((2u * dl) << 8) | ((2u * dl + 1u) << 12)) : (dl << 4);
+        span_ = static_cast<uint32_t>(sizeof(T)) * (1u + dl);
+        selb0_ = sizeof(T) == 2 ? 0x7410u : 0x7440u;
+        selb1_ = sizeof(T) == 2 ? 0x7432u : 0x7441u;
+      } else {
+        psel_c_ = span_ = 0;
+      }
     }
     vmax_ = 0;
     for (int i = 0; i < 12; ++i) acc_[i] = 0;
@@ -525,8 +546,18 @@ struct Strip {
       asm volatile("cp.async.commit_group;" ::: "memory");  // an empty group keeps the wait counts
       return;
     }
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n\tcp.async.commit_group;" ::"r"(dst), "l"(p0_ + off)
-                 : "memory");
+    if constexpr (kTwoWord) {
+      const unsigned char *a = p0_ + off;
+      const uint32_t o = static_cast<uint32_t>(reinterpret_cast<uintptr_t>(a)) & 3u;
+      const unsigned char *w = a - o;  // the aligned word holding the first pixel
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst), "l"(w) : "memory");
+      if (o + span_ > 4u)  // the pixels run into the next word
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst + kRing2Off), "l"(w + 4) : "memory");
+      asm volatile("cp.async.commit_group;" ::: "memory");
+    } else {
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n\tcp.async.commit_group;" ::"r"(dst), "l"(p0_ + off)
+                   : "memory");
+    }
   }
   __device__ __forceinline__ void async_drain() {
     if constexpr (kAsync) asm volatile("cp.async.wait_group 0;" ::: "memory");
@@ -605,6 +636,17 @@ struct Strip {
         if (FX_GUARD(ring_h_ + 128u * S - ring_base_ < 128u * kRingRows))
           asm volatile("cp.async.wait_group 6;\n\tld.shared.u32 %0, [%1];" : "=r"(r0) : "r"(ring_h_ + 128u * S) : "memory");
         r1 = r0;
+        if constexpr (kTwoWord) {
+          // the row's byte offset (its load clamped the row the same way)
+          uint32_t w1 = 0;
+          if (FX_GUARD(ring_h_ + 128u * S - ring_base_ < 128u * kRingRows))
+            asm volatile("ld.shared.u32 %0, [%1];" : "=r"(w1) : "r"(ring_h_ + 128u * S + kRing2Off) : "memory");
+          const int32_t yr = t < rlo ? rlo : (t > rhi ? rhi : t);
+          const uint32_t o = (static_cast<uint32_t>(reinterpret_cast<uintptr_t>(p0_)) +
+                              static_cast<uint32_t>(yr - rbase) * pitch32) & 3u;
+          r0 = __byte_perm(r0, w1, psel_c_ + o * 0x1111u);  // the pixels as a pair word
+          r1 = r0;
+        }
         // refill the slot of row t - 1 (read one step ago) with row t + 7
         load_row_async<kChk>(S == 0 ? ring_o_ + 384u : ring_h_ + 128u * (S - 1), t + kRingRows - 1);
       } else {
@@ -612,8 +654,8 @@ struct Strip {
         r1 = raw1_[S];
       }
       const uint32_t b2 = __byte_perm(r0, 0x4B000000u, selb0_);
-      const uint32_t b3 = __byte_perm(kPair ? r0 : r1, 0x4B000000u, selb1_);
-      if (checking()) track_max(kPair ? r0 : __byte_perm(r0, r1, 0x5410));
+      const uint32_t b3 = __byte_perm(kPair || kTwoWord ? r0 : r1, 0x4B000000u, selb1_);
+      if (checking()) track_max(kPair || kTwoWord ? r0 : __byte_perm(r0, r1, 0x5410));
       if constexpr (!kAsync) load_row<S, kChk>(t + 4);
       const uint32_t b0 = __shfl_up_sync(kFull, b2, 1), b1 = __shfl_up_sync(kFull, b3, 1);
       const uint32_t b4 = __shfl_down_sync(kFull, b2, 1), b5 = __shfl_down_sync(kFull, b3, 1);
@@ -1121,7 +1163,7 @@ __device__ __forceinline__ uint8_t *unit_marker(const ImageView &v, int64_t ux, 
 
 // Per-warp shared words of the streaming path (the caller's kernel owns one
 // array of this type per CTA and passes the warp's slice).
-constexpr int kStripWords = 40;  // 32 block words + the 8-row input ring
+constexpr int kStripWords = 48;  // 32 block words + two 8-row input rings
 using StripWords = uint32_t[kWarpsPerCta][kStripWords][32];
 __device__ __forceinline__ uint32_t (*warp_words(StripWords &w))[32] { return w[(threadIdx.x >> 5) % kWarpsPerCta]; }
 
@@ -1134,7 +1176,7 @@ __device__ __forceinline__ void fast_unit(const ImageView &v, const KParams &kp,
                                           int uh, uint32_t (*words)[32]) {
   constexpr int kMode = kF32Log ? st::kModeF32Log : st::kModeF32;
   using S = st::Strip<T, kMode, kPair, kSd2, kSrcZ, kRm, Cst>;
-  static_assert(S::kWords + S::kRingRows == kStripWords, "shared word layout");
+  static_assert(S::kWords + 2 * S::kRingRows == kStripWords, "shared word layout");
   if (kp.fbound < 0) return;
   constexpr int uw = strip_width(kSrcZ, kRm);
   const int64_t X0 = ux * uw;
