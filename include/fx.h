@@ -311,10 +311,11 @@ fx_status fx_extract_batch_noalloc(const fx_params *params, const fx_image_desc 
  * Compiles, at run time on the current device, fx_extract's streaming first
  * pass for this parameter set and dtype with the two LoG masks' ring weights
  * and the contrast thresholds as compile-time constants (NVRTC; a second or
- * two per call, cached for the life of the process).  Afterwards fx_extract
- * and the host-buffer entry points use that kernel whenever their parameters
- * match and the image is read as aligned words (base and pitch multiples of
- * 4 bytes); other calls use the library's precompiled kernels.  The masks are
+ * two per call, cached for the life of the process); likewise the batched
+ * path's group kernels.  Afterwards fx_extract and the host-buffer entry
+ * points use these kernels whenever their parameters match, and so do the
+ * graphs of plans created afterwards; other calls use the library's
+ * precompiled kernels.  The masks are
  * identical either way (the same operations, in the same order).  A tuning
  * aid of this library; the paper has no counterpart.
  * Errors: FX_ERR_INVALID_ARG, FX_ERR_RANGE; FX_ERR_UNSUPPORTED when the

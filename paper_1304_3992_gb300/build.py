@@ -82,7 +82,7 @@ def build(force: bool = False, verbose: bool = False, extra: list[str] | None = 
     with cf.ThreadPoolExecutor(max_workers=max(1, min(len(srcs), os.cpu_count() or 4))) as ex:
         objs = list(ex.map(lambda s: _compile(s, extra, build_dir), srcs))
     tmp = lib + f".{os.getpid()}.tmp"
-    cmd = ["nvcc", ARCH, "-shared", "-cudart", "static", "-o", tmp, *objs, "-ldl"]
+    cmd = ["nvcc", ARCH, "-shared", "-cudart", "static", "-o", tmp, *objs, "-ldl", "-lpthread"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed: {' '.join(cmd)}\n{r.stdout}\n{r.stderr}")

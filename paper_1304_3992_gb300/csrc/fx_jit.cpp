@@ -8,9 +8,9 @@
 // with NVRTC, the weights and thresholds of one parameter set being
 // compile-time constants (instruction immediates), and caches the kernel per
 // device, pixel size, load path, strip class and constants; it does the same
-// for the batched path's group kernel (fx::batch_kernel_fast).  fx_extract and
-// the host-buffer path launch it whenever their parameters match, and plans
-// created afterwards put it in their graphs; the
+// for the batched path's group kernel (fx::batch_kernel_fast), each for both
+// load paths.  fx_extract and the host-buffer path launch them whenever their
+// parameters match, and plans created afterwards put them in their graphs; the
 // arithmetic is the same, so the masks are identical either way.  NVRTC is
 // loaded on first use (dlopen); without it fx_specialize reports
 // FX_ERR_UNSUPPORTED and every call runs the precompiled kernels.
@@ -22,6 +22,7 @@
 #include <map>
 #include <mutex>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "fx_internal.h"
@@ -211,33 +212,42 @@ const void *lookup(int kind, const KParams &kp, int elem, bool pair, int rm_clas
 const void *specialized_kernel(const KParams &kp, int elem, bool pair, int rm_class) {
   return lookup(0, kp, elem, pair, rm_class);
 }
-const void *specialized_batch_kernel(const KParams &kp, int elem, int rm_class) {
-  return lookup(1, kp, elem, true, rm_class);
+const void *specialized_batch_kernel(const KParams &kp, int elem, bool pair, int rm_class) {
+  return lookup(1, kp, elem, pair, rm_class);
 }
 
-// Compiles the pair-load first pass of fx_extract and of the batched path for
-// kp (the load path of images whose base and pitch are multiples of 4 bytes)
-// on the current device.
+// Compiles the first pass of fx_extract and the batched group kernel for kp,
+// each for both load paths (aligned words, and rows that are not 4-byte
+// aligned), on the current device; the four compiles run in parallel.
 fx_status specialize(const KParams &kp, int elem) {
   if (checked_build()) return FX_ERR_UNSUPPORTED;  // its kernels count range-check failures
   if (kp.fbound < 0 || !fast_path_supported(kp)) return FX_ERR_UNSUPPORTED;
   if (!nvrtc().ok) return FX_ERR_UNSUPPORTED;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return FX_ERR_CUDA;
-  for (int kind = 0; kind < 2; ++kind) {
-    const Variant v = variant_of(kind, dev, kp, elem, true, strip_class(kp));
-    const std::string key = key_of(v);
-    {
+  std::vector<Variant> todo;
+  for (int kind = 0; kind < 2; ++kind)
+    for (int pair = 1; pair >= 0; --pair) {
+      const Variant v = variant_of(kind, dev, kp, elem, pair != 0, strip_class(kp));
       std::lock_guard<std::mutex> lock(g_mu);
-      if (g_cache.count(key)) continue;
+      if (!g_cache.count(key_of(v))) todo.push_back(v);
     }
-    const void *k = build(v);
-    if (!k) return FX_ERR_UNSUPPORTED;
-    std::lock_guard<std::mutex> lock(g_mu);
-    g_cache[key] = k;
-    __atomic_store_n(&g_entries, static_cast<int>(g_cache.size()), __ATOMIC_RELEASE);
+  std::vector<const void *> built(todo.size(), nullptr);
+  std::vector<std::thread> threads;
+  for (size_t i = 0; i < todo.size(); ++i)
+    threads.emplace_back([&, i] {
+      // each thread loads its cubin on the caller's device
+      if (cudaSetDevice(dev) == cudaSuccess) built[i] = build(todo[i]);
+    });
+  for (auto &t : threads) t.join();
+  std::lock_guard<std::mutex> lock(g_mu);
+  bool all = true;
+  for (size_t i = 0; i < todo.size(); ++i) {
+    if (built[i]) g_cache[key_of(todo[i])] = built[i];
+    else all = false;
   }
-  return FX_OK;
+  __atomic_store_n(&g_entries, static_cast<int>(g_cache.size()), __ATOMIC_RELEASE);
+  return all ? FX_OK : FX_ERR_UNSUPPORTED;
 }
 
 }  // namespace fx

@@ -184,10 +184,11 @@ fx_status build_graph(fx_plan *p, int i) {
       void *gargs[] = {&tab, &ctr, &stp, kg};
       cudaKernelNodeParams kf = kn;
       kf.func = const_cast<void *>(plan_fast_kernel(p->rm_class, p->kp8, gi));
-      // the aligned-load groups: a kernel compiled for the plan's parameters, if any (fx_specialize)
-      if (gi < 2)
-        if (const void *jk = specialized_batch_kernel(gi == 0 ? p->kp16 : p->kp8, gi == 0 ? 2 : 1, p->rm_class))
-          kf.func = const_cast<void *>(jk);
+      // a kernel compiled for the plan's parameters, if any (fx_specialize); groups 0 / 1
+      // hold the aligned-load images, 2 / 3 the others
+      if (const void *jk = specialized_batch_kernel(gi % 2 == 1 ? p->kp8 : p->kp16, gi % 2 == 1 ? 1 : 2, gi < 2,
+                                                    p->rm_class))
+        kf.func = const_cast<void *>(jk);
       kf.kernelParams = gargs;
       e = cudaGraphAddKernelNode(&n_grp[gi], g, &n_zero, 1, &kf);
     }

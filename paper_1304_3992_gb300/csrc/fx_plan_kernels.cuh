@@ -68,7 +68,7 @@ __device__ inline ImageView view_of(const BatchImage &b) {
 const void *plan_fast_kernel(int rm_class, const KParams &kp, int g);
 const void *plan_redo_kernel(int rm_class, const KParams &kp);
 // group kernel compiled at run time for kp (fx_specialize), or nullptr (fx_jit.cpp)
-const void *specialized_batch_kernel(const KParams &kp, int elem, int rm_class);
+const void *specialized_batch_kernel(const KParams &kp, int elem, bool pair, int rm_class);
 #endif
 
 // One group of the streaming path (load path kPair, pixel type T): its units
