@@ -244,13 +244,19 @@ def run_stream(server: Server, images, rate_hz: float, duration_s: float, seed: 
 class TorchBackend:
     """GPU backend: torch device buffers, a copy stream, one plan + stream per slot."""
 
-    def __init__(self, params, slots: int = 2, max_images: int = 64, device: int = 0):
+    def __init__(self, params, slots: int = 2, max_images: int = 64, device: int = 0, specialize: bool = True):
         import torch
         from . import fx
         self.torch, self.fx = torch, fx
         self.device = torch.device("cuda", device)
         self.copy_stream = torch.cuda.Stream(self.device)
         self.streams = [torch.cuda.Stream(self.device) for _ in range(slots)]
+        # kernels compiled for the served parameters before the plans are made
+        # (fx_specialize; a no-op where run-time compilation is unavailable)
+        self.specialized = False
+        if specialize:
+            with torch.cuda.device(self.device):
+                self.specialized = fx.specialize(params, fx.FX_U16) and fx.specialize(params, fx.FX_U8)
         self.plans = [fx.Plan(params, max_images=max_images, device=device) for _ in range(slots)]
 
     def alloc(self, image):
