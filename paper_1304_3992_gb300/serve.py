@@ -256,7 +256,11 @@ class TorchBackend:
         self.specialized = False
         if specialize:
             with torch.cuda.device(self.device):
-                self.specialized = fx.specialize(params, fx.FX_U16) and fx.specialize(params, fx.FX_U8)
+                for dt in (fx.FX_U16, fx.FX_U8):
+                    try:  # parameters that a dtype cannot evaluate exactly stay on the precompiled kernels
+                        self.specialized = fx.specialize(params, dt) or self.specialized
+                    except fx.FxError:
+                        pass
         self.plans = [fx.Plan(params, max_images=max_images, device=device) for _ in range(slots)]
 
     def alloc(self, image):
