@@ -214,17 +214,19 @@ fx_status fx_extract_batch(fx_plan *plan, const fx_image_desc *descs, int32_t n,
  * median or one window-3 median, 52 while the median radii add up to at most
  * 3 (the default window 5 included), 44 up to 7; 4 fewer when the standard
  * deviation is taken over the crossing map.  tile_h is a multiple
- * of 16 in [16, 8192], or 0; ctas_per_sm is in 1..8 (4 warps per CTA).
+ * of 16 in [16, 8192], or 0; ctas_per_sm is in 1..32 (one warp per CTA on
+ * the streaming kernels, 256 threads on the general kernel).
  * A new plan picks the unit height for each batch itself (multiples of 16 up
- * to 1024, from the batch's unit count against the resident warps; 3 CTAs
+ * to 1024, from the batch's unit count against the resident warps; 12 CTAs
  * per SM) until one of the two calls below fixes another shape.
  * fx_plan_autotune times the automatic height and the heights
- * {256, 512, 768, 1024} x every CTAs-per-SM count the kernel's occupancy
- * allows on the given images (their outputs are overwritten) and keeps the
- * fastest; fx_plan_set_tile forces one.  In both calls tile_h 0 stands for the
+ * {256, 512, 768, 1024} x three CTAs-per-SM counts (12, 10 and 8 on the
+ * streaming kernels; 1 .. 8 as the general kernel's occupancy allows) on the
+ * given images (their outputs are overwritten) and keeps the fastest;
+ * fx_plan_set_tile forces one.  In both calls tile_h 0 stands for the
  * automatic height (picked per batch for the given CTAs per SM).  Plans whose
  * parameters need the general kernel (median windows whose radii add up to
- * more than 3) use its fixed 64 x 32 tile; for them
+ * more than 7) use its fixed 64 x 32 tile; for them
  * only ctas_per_sm takes effect.
  * Errors: FX_ERR_INVALID_ARG (shape or count out of range), FX_ERR_CUDA.
  */

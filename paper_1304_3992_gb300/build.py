@@ -52,7 +52,7 @@ def _compile(src: str, extra: list[str], build_dir: str = BUILD) -> str:
     obj = os.path.join(build_dir, os.path.basename(src) + ".o")
     inc = ["-I" + os.path.join(ROOT, "include"), "-I" + CSRC]
     if src.endswith(".cu"):
-        extra = extra + [f"-D{k}={os.environ[k]}" for k in ("FX_FIRST_PASS_CTAS", "FX_WARPS_PER_CTA") if os.environ.get(k)]
+        extra = extra + [f"-D{k}={os.environ[k]}" for k in ("FX_FIRST_PASS_CTAS", "FX_WARPS_PER_CTA", "FX_BATCH_CTAS") if os.environ.get(k)]
         cmd = ["nvcc", ARCH, "-lineinfo", "-O3", "-std=c++17", "-Xcompiler", "-fPIC",
                "-Xcompiler", "-ffp-contract=off", "--expt-relaxed-constexpr", *inc, *extra,
                "-c", src, "-o", obj]
@@ -61,7 +61,7 @@ def _compile(src: str, extra: list[str], build_dir: str = BUILD) -> str:
         # source tree and the toolkit's libnvrtc
         paths = [f'-DFX_SRC_DIR="{CSRC}"', f'-DFX_INC_DIR="{os.path.join(ROOT, "include")}"',
                  f'-DFX_CUDA_LIB_DIR="{os.path.join(_cuda_home(), "lib64")}"']
-        extra = extra + [f"-D{k}={os.environ[k]}" for k in ("FX_FIRST_PASS_CTAS", "FX_WARPS_PER_CTA") if os.environ.get(k)]
+        extra = extra + [f"-D{k}={os.environ[k]}" for k in ("FX_FIRST_PASS_CTAS", "FX_WARPS_PER_CTA", "FX_BATCH_CTAS") if os.environ.get(k)]
         cmd = ["g++", "-O2", "-std=c++17", "-fPIC", "-ffp-contract=off", "-fno-fast-math",
                "-I" + os.path.join(_cuda_home(), "include"), *inc, *paths, *extra, "-c", src, "-o", obj]
     r = subprocess.run(cmd, capture_output=True, text=True)

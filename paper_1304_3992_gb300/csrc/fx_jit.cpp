@@ -169,6 +169,9 @@ const void *build(const Variant &v) {
 #ifdef FX_FIRST_PASS_CTAS
   opts.push_back("-DFX_FIRST_PASS_CTAS=" + std::to_string(FX_FIRST_PASS_CTAS));
 #endif
+#ifdef FX_BATCH_CTAS
+  opts.push_back("-DFX_BATCH_CTAS=" + std::to_string(FX_BATCH_CTAS));
+#endif
   std::vector<const char *> argv;
   for (const auto &o : opts) argv.push_back(o.c_str());
   n.add_name(prog, name.c_str());

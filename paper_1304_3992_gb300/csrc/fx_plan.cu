@@ -332,7 +332,7 @@ fx_status fx_plan_create(fx_plan **out, const fx_params *params, int32_t max_ima
   p->max_images = max_images;
   p->unit_w = strip_width(p->kp8.source == 1, p->rm_class);
   p->unit_h = kDefaultUnitH;
-  p->ctas_per_sm = p->fast ? kFirstPassCtas : 2;
+  p->ctas_per_sm = p->fast ? kBatchCtas : 2;
   p->auto_h = true;
   DeviceScope dev(device);
   if (!dev.ok || cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
@@ -411,7 +411,7 @@ fx_status fx_extract_batch(fx_plan *p, const fx_image_desc *descs, int32_t n, vo
 }
 
 fx_status fx_plan_set_tile(fx_plan *p, int32_t tile_w, int32_t tile_h, int32_t ctas_per_sm) {
-  if (!p || ctas_per_sm < 1 || ctas_per_sm > 8) return FX_ERR_INVALID_ARG;
+  if (!p || ctas_per_sm < 1 || ctas_per_sm > kMaxCtasPerSm) return FX_ERR_INVALID_ARG;
   // tile_h 0: the height is picked per batch (the wave model in fill_table)
   const bool automatic = tile_h == 0;
   const int th = automatic ? kDefaultUnitH : tile_h;
@@ -443,7 +443,11 @@ fx_status fx_plan_autotune(fx_plan *p, const fx_image_desc *descs, int32_t n, vo
   // candidates: the automatic height (0), then the fixed heights
   for (int c = -1; c < kNumUnitHeights && st == FX_OK; ++c) {
     const int uw = strip_width(p->kp8.source == 1, p->rm_class), uh = c < 0 ? 0 : kUnitHeights[c];
-    for (int cps = 1; cps <= kMaxCtasPerSm && st == FX_OK; ++cps) {
+    // CTAs per SM: the streaming kernels' default and two and four fewer, the
+    // general kernel's 1 .. 8 (its occupancy decides)
+    const int cands_fast[3] = {kBatchCtas, std::max(1, kBatchCtas - 2), std::max(1, kBatchCtas - 4)};
+    for (int ci = 0; ci < (p->fast ? 3 : 8) && st == FX_OK; ++ci) {
+      const int cps = p->fast ? cands_fast[ci] : ci + 1;
       if (!p->fast && uh != 0) continue;
       if ((st = fx_plan_set_tile(p, uw, uh, cps)) != FX_OK) break;
       int occ = 0;

@@ -78,7 +78,7 @@ const void *specialized_batch_kernel(const KParams &kp, int elem, bool pair, int
 // Cst: as for fx_extract's first pass (RuntimeConsts, or the constants of a
 // kernel compiled at run time for one parameter set).
 template <typename T, bool kF32Log, bool kPair, bool kSd2, bool kSrcZ, int kRm, class Cst = RuntimeConsts>
-__global__ void __launch_bounds__(32 * kWarpsPerCta, kFirstPassCtas) batch_kernel_fast(const unsigned char *table,
+__global__ void __launch_bounds__(32 * kWarpsPerCta, kBatchCtas) batch_kernel_fast(const unsigned char *table,
                                                                       unsigned long long *counter, int *status,
                                                                       const __grid_constant__ KParams kp) {
   __shared__ StripWords words;

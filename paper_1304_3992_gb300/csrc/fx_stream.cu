@@ -31,12 +31,12 @@ bool pair_loads_ok(const void *img, int64_t width, int64_t pitch, int64_t elem) 
 }
 bool pair_loads_ok(const ImageView &v) { return pair_loads_ok(v.img, v.width, v.pitch, v.elem); }
 
-// Resident warps of the streaming kernel on the current device (3 CTAs of 4
-// warps per SM), cached per device.
+// Resident warps of the streaming kernel on the current device
+// (kFirstPassCtas CTAs of kWarpsPerCta warps per SM), cached per device.
 int64_t warp_slots() {
   static int64_t slots[64] = {};
   int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 152 * 12;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 152 * kFirstPassCtas * kWarpsPerCta;
   if (!slots[dev]) {
     int sms = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 152;

@@ -63,17 +63,29 @@ constexpr int kDefaultUnitH = 512;
 // unit heights the batched plan's autotuner times
 constexpr int kNumUnitHeights = 4;
 constexpr int kUnitHeights[kNumUnitHeights] = {256, 512, 768, 1024};
-constexpr int kMaxCtasPerSm = 8;
+constexpr int kMaxCtasPerSm = 32;
+// Warps per CTA of the streaming kernels and CTAs per SM of the first pass
+// (its __launch_bounds__ and the wave model of the unit height).  One-warp
+// CTAs, 13 per SM: a warp's slot frees when its own unit ends, and under the
+// bound of 13 x 32 threads the compiler keeps the strip in about 127
+// registers without spill.  Measured on a 16384^2 band (specialised kernel):
+// 1 x 13 251.8 Gpx/s, 1 x 14 248.3, 1 x 16 249.2, 1 x 12 243.4, 2 x 7 225.0,
+// 4 x 3 227.4, 4 x 4 220.4.
 #ifndef FX_WARPS_PER_CTA
-#define FX_WARPS_PER_CTA 4
+#define FX_WARPS_PER_CTA 1
 #endif
 constexpr int kWarpsPerCta = FX_WARPS_PER_CTA;
-// CTAs per SM of the streaming first pass (its __launch_bounds__ and the wave
-// model of the unit height)
 #ifndef FX_FIRST_PASS_CTAS
-#define FX_FIRST_PASS_CTAS 3
+#define FX_FIRST_PASS_CTAS 13
 #endif
 constexpr int kFirstPassCtas = FX_FIRST_PASS_CTAS;
+// The batched group kernels carry their queue loop as well: at 13 warps per
+// SM (four on some scheduler, so 128 registers) they spill, at 12 (168
+// registers) they do not.
+#ifndef FX_BATCH_CTAS
+#define FX_BATCH_CTAS 12
+#endif
+constexpr int kBatchCtas = FX_BATCH_CTAS;
 
 // Where the first pass takes the LoG ring weights and the contrast threshold
 // from: the kernel parameters (RuntimeConsts), or, in a kernel compiled at run
@@ -1189,8 +1201,8 @@ __device__ __forceinline__ void fast_unit(const ImageView &v, const KParams &kp,
 }
 
 // The streaming first pass of fx_extract: one unit per warp, units in
-// row-band order (unit = CTA * kWarpsPerCta + warp; ux = unit % units_x).  3
-// CTAs (12 warps) per SM in 168 registers.
+// row-band order (unit = CTA * kWarpsPerCta + warp; ux = unit % units_x),
+// kFirstPassCtas CTAs per SM.
 template <typename T, bool kF32Log, bool kPair, bool kSd2, bool kSrcZ, int kRm, class Cst>
 __global__ void __launch_bounds__(32 * kWarpsPerCta, kFirstPassCtas)
     stream_kernel(const __grid_constant__ ImageView v, const __grid_constant__ KParams kp, int64_t units_x,

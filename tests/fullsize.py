@@ -12,8 +12,8 @@ from __future__ import annotations
 
 import numpy as np
 
-FIRST_PASS_CTAS = 3   # CTAs of 4 warps per SM of the streaming first pass
-WARPS_PER_CTA = 4
+FIRST_PASS_CTAS = 13  # one-warp CTAs per SM of the streaming first pass
+WARPS_PER_CTA = 1
 
 
 def strip_width(r_m: int, source: int = 0) -> int:

@@ -230,14 +230,14 @@ def test_ms8192_u16_sampled_rows(cuda_lib):
 
 def test_band16384_u16_unit_seams_all_bands(cuda_lib):
     """The benchmark's four 16384^2 12-bit bands, each in the benchmark's
-    launch configuration: 40-row bands across the first three unit seams (720
+    launch configuration: 40-row bands across the first three unit seams (656
     rows apart on 152 SMs), the top and bottom rows and one random band,
     against the oracle."""
     import fullsize
     sms = torch.cuda.get_device_properties(0).multi_processor_count
     uh = fullsize.unit_height(16384, 16384, sms)
     if sms == 152:
-        assert uh == 720
+        assert uh == 656
     d, p = pair(16.0)
     for b, band in enumerate(scenes.ms_bands_u16_12bit()):
         got = run(cuda_lib, band, p)
