@@ -384,7 +384,7 @@ def test_batch_autotune_keeps_results(cuda_lib):
     singles = [run(cuda_lib, img, p) for img, _ in pairs]
     with cuda_lib.Plan(p, max_images=8) as plan:
         cfg = plan.autotune(pairs)
-        assert cfg[2] >= 1
+        assert cfg[2] in (12, 10, 8)  # the streaming group kernels' candidates
         for o in pairs:
             o[1].zero_()
         plan.extract_batch(pairs)
@@ -401,7 +401,9 @@ def test_batch_set_tile_shapes_keep_results(cuda_lib):
     pairs = [(dev_pitched(v, v.strides[0]), torch.zeros(v.shape, dtype=torch.uint8, device="cuda")) for v, _ in batch]
     singles = [run(cuda_lib, img, p) for img, _ in pairs]
     with cuda_lib.Plan(p, max_images=8) as plan:
-        for shape in [(52, 16, 1), (52, 1024, 2), (52, 0, 3), (52, 0, 1)]:
+        # one-warp CTAs: 1 .. 32 per SM; 24 exceeds the resident count (the
+        # CTAs beyond it start when earlier ones exit and find the queue empty)
+        for shape in [(52, 16, 1), (52, 1024, 2), (52, 0, 3), (52, 0, 1), (52, 0, 12), (52, 512, 24)]:
             plan.set_tile(*shape)
             for o in pairs:
                 o[1].fill_(9)
