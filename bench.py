@@ -487,7 +487,8 @@ def bench_variants(fx, torch, stream, band, out, band_np, reps=5):
         "median_7": (dict(hmf=(7,)), "streaming"),
         "median_5_then_5": (dict(hmf=(5, 5)), "streaming, wide strips"),
         "median_7_5_3": (dict(hmf=(7, 5, 3)), "streaming, wide strips"),
-        "median_7_7_7": (dict(hmf=(7, 7, 7)), "general tile"),
+        "median_7_7_7": (dict(hmf=(7, 7, 7)), "streaming, extra-wide strips"),
+        "median_7_7_7_7": (dict(hmf=(7, 7, 7, 7)), "general tile"),
         "stddev_over_crossing_map": (dict(stddev_source=1, t_sd5=(0.2, 0.3), t_sdmax=(0.45, 0.5),
                                           t_sd3=(0.3, 0.4)), "streaming"),
     }

@@ -93,7 +93,7 @@ typedef struct {
   /* Hybrid-median windows applied in order (3, 5 or 7; 0 ends the list;
    * Sec. 3.4 leaves the size to the application, Sec. 4.2 repeats the filter
    * with several sizes).  Default {5, 0, 0, 0}; all zero switches the filter
-   * off.  fx_extract runs lists whose radii (window / 2) add up to at most 7
+   * off.  fx_extract runs lists whose radii (window / 2) add up to at most 11
    * in its fused streaming kernel, longer ones in the general tile kernel. */
   int32_t hmf[FX_MAX_HMF_LEVELS];
   /* Nominal radiometric depth used only to scale the default thresholds
@@ -191,8 +191,8 @@ typedef struct {
  * persistent kernels pop work units from a tile queue (one kernel per load
  * path and pixel type on the streaming path, then the redo pass), the batched
  * form of Sec. 6.2.2's one-thread-per-pixel mapping.  Median lists whose radii
- * add up to at most 7 run on the streaming strips of fx_extract (compact,
- * narrow or wide), longer lists on the general tile kernel.  Each image's
+ * add up to at most 11 run on the streaming strips of fx_extract (compact,
+ * narrow, wide or extra wide), longer lists on the general tile kernel.  Each image's
  * mask is byte-identical to fx_extract's.  descs is a HOST array of n descriptors, validated like
  * fx_extract's arguments; the table is copied before the call returns.
  * Output masks must not overlap each other or any input.
@@ -212,8 +212,8 @@ fx_status fx_extract_batch(fx_plan *plan, const fx_image_desc *descs, int32_t n,
  * strip of tile_w output columns by tile_h output rows walked by one warp;
  * tile_w must be the strip width of the plan's streaming strips: 56 with no
  * median or one window-3 median, 52 while the median radii add up to at most
- * 3 (the default window 5 included), 44 up to 7; 4 fewer when the standard
- * deviation is taken over the crossing map.  tile_h is a multiple
+ * 3 (the default window 5 included), 44 up to 7, 36 up to 11; 4 fewer when
+ * the standard deviation is taken over the crossing map.  tile_h is a multiple
  * of 16 in [16, 8192], or 0; ctas_per_sm is in 1..32 (one warp per CTA on
  * the streaming kernels, 256 threads on the general kernel).
  * A new plan picks the unit height for each batch itself (multiples of 16 up
@@ -226,7 +226,7 @@ fx_status fx_extract_batch(fx_plan *plan, const fx_image_desc *descs, int32_t n,
  * fx_plan_set_tile forces one.  In both calls tile_h 0 stands for the
  * automatic height (picked per batch for the given CTAs per SM).  Plans whose
  * parameters need the general kernel (median windows whose radii add up to
- * more than 7) use its fixed 64 x 32 tile; for them
+ * more than 11) use its fixed 64 x 32 tile; for them
  * only ctas_per_sm takes effect.
  * Errors: FX_ERR_INVALID_ARG (shape or count out of range), FX_ERR_CUDA.
  */

@@ -340,6 +340,7 @@ namespace fx {
 // check counters of the batched path's compact and wide kernels (fx_plan_compact.cu, fx_plan_wide.cu)
 unsigned long long checked_count_plan_compact(bool reset);
 unsigned long long checked_count_plan_wide(bool reset);
+unsigned long long checked_count_plan_xwide(bool reset);
 }  // namespace fx
 
 extern "C" fx_status fx_checked_violations(uint64_t *count, int32_t reset) {
@@ -350,6 +351,7 @@ extern "C" fx_status fx_checked_violations(uint64_t *count, int32_t reset) {
   unsigned long long (*const readers[])(bool) = {fx::checked_count_stream, fx::checked_count_stream_wide,
                                                   fx::checked_count_stream_compact,
                                                   fx::checked_count_tile, fx::checked_count_plan, fx::checked_count_plan_compact, fx::checked_count_plan_wide,
+                                                  fx::checked_count_plan_xwide, fx::checked_count_stream_xwide,
                                                   fx::checked_count_noalloc, fx::checked_count_hmf};
   uint64_t total = 0;
   for (auto r : readers) {

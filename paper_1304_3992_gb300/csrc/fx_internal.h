@@ -103,18 +103,21 @@ cudaError_t launch_tile_general(const ImageView &v, const KParams &kp, cudaStrea
 unsigned long long checked_count_stream(bool reset);
 unsigned long long checked_count_stream_wide(bool reset);
 unsigned long long checked_count_stream_compact(bool reset);
+unsigned long long checked_count_stream_xwide(bool reset);
 unsigned long long checked_count_tile(bool reset);
 unsigned long long checked_count_plan(bool reset);
 unsigned long long checked_count_noalloc(bool reset);
 unsigned long long checked_count_hmf(bool reset);
 bool checked_build();
-bool fast_path_supported(const KParams &kp);  // the streaming kernels (compact, narrow or wide strips)
+bool fast_path_supported(const KParams &kp);  // the streaming kernels (compact, narrow, wide or extra-wide strips)
 bool stream_narrow(const KParams &kp);        // the narrow strips serve it (also the batched kernels)
 int strip_class(const KParams &kp);           // the smallest strip class that serves kp (its median radius sum)
 cudaError_t launch_compact(const ImageView &v, const KParams &kp, cudaStream_t s, int64_t blocks, int64_t units_x,
                            int64_t units, int uh);
 cudaError_t launch_wide(const ImageView &v, const KParams &kp, cudaStream_t s, int64_t blocks, int64_t units_x,
                         int64_t units, int uh);
+cudaError_t launch_xwide(const ImageView &v, const KParams &kp, cudaStream_t s, int64_t blocks, int64_t units_x,
+                         int64_t units, int uh);
 bool pair_loads_ok(const ImageView &v);
 bool pair_loads_ok(const void *img, int64_t width, int64_t pitch, int64_t elem);
 cudaError_t launch_fast(const ImageView &v, const KParams &kp, cudaStream_t s);

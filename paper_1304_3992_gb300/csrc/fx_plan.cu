@@ -47,23 +47,27 @@ __global__ void __launch_bounds__(256) batch_kernel_general(const unsigned char 
 
 }  // namespace
 
-// The narrow class's selectors (the compact and wide classes are in
-// fx_plan_compact.cu and fx_plan_wide.cu).
+// The narrow class's selectors (the other classes are in fx_plan_compact.cu,
+// fx_plan_wide.cu and fx_plan_xwide.cu).
 const void *plan_fast_kernel_narrow(const KParams &kp, int g) { return fast_kernel_of<kNarrowRm>(kp, g); }
 const void *plan_redo_kernel_narrow(const KParams &kp) { return redo_kernel_of<kNarrowRm>(kp); }
 const void *plan_fast_kernel_compact(const KParams &kp, int g);
 const void *plan_redo_kernel_compact(const KParams &kp);
 const void *plan_fast_kernel_wide(const KParams &kp, int g);
 const void *plan_redo_kernel_wide(const KParams &kp);
+const void *plan_fast_kernel_xwide(const KParams &kp, int g);
+const void *plan_redo_kernel_xwide(const KParams &kp);
 
 const void *plan_fast_kernel(int rm_class, const KParams &kp, int g) {
   if (rm_class == kCompactRm) return plan_fast_kernel_compact(kp, g);
   if (rm_class == kWideRm) return plan_fast_kernel_wide(kp, g);
+  if (rm_class == kXWideRm) return plan_fast_kernel_xwide(kp, g);
   return plan_fast_kernel_narrow(kp, g);
 }
 const void *plan_redo_kernel(int rm_class, const KParams &kp) {
   if (rm_class == kCompactRm) return plan_redo_kernel_compact(kp);
   if (rm_class == kWideRm) return plan_redo_kernel_wide(kp);
+  if (rm_class == kXWideRm) return plan_redo_kernel_xwide(kp);
   return plan_redo_kernel_narrow(kp);
 }
 

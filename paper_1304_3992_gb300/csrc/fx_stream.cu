@@ -9,11 +9,13 @@ namespace fx {
 // The streaming kernels cover both standard-deviation sources and up to four
 // median passes: compact strips while the median radii add up to at most 1
 // (halo: 2 LoG + 1 crossing (+ 2 crossing-map deviation) + 1 median column),
-// narrow strips up to 3, wide strips up to 7.  The batched plans use the
+// narrow strips up to 3, wide strips up to 7, extra-wide strips up to 11.  The batched plans use the
 // narrow strips only.
 bool stream_narrow(const KParams &kp) { return kp.nhmf <= FX_MAX_HMF_LEVELS && kp.r_m <= kNarrowRm; }
-bool fast_path_supported(const KParams &kp) { return kp.nhmf <= FX_MAX_HMF_LEVELS && kp.r_m <= kWideRm; }
-int strip_class(const KParams &kp) { return kp.r_m <= kCompactRm ? kCompactRm : kp.r_m <= kNarrowRm ? kNarrowRm : kWideRm; }
+bool fast_path_supported(const KParams &kp) { return kp.nhmf <= FX_MAX_HMF_LEVELS && kp.r_m <= kXWideRm; }
+int strip_class(const KParams &kp) {
+  return kp.r_m <= kCompactRm ? kCompactRm : kp.r_m <= kNarrowRm ? kNarrowRm : kp.r_m <= kWideRm ? kWideRm : kXWideRm;
+}
 
 // One aligned load per lane and row: base and pitch multiples of 4 bytes.
 // uint16: an even width or a row pitch with room for one more pixel, so that
@@ -81,6 +83,7 @@ cudaError_t launch_fast(const ImageView &v, const KParams &kp, cudaStream_t s) {
   const int64_t blocks = (units + kWarpsPerCta - 1) / kWarpsPerCta;
   if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
   if (rm_class == kWideRm) return launch_wide(v, kp, s, blocks, units_x, units, uh);
+  if (rm_class == kXWideRm) return launch_xwide(v, kp, s, blocks, units_x, units, uh);
   if (rm_class == kCompactRm) return launch_compact(v, kp, s, blocks, units_x, units, uh);
   return v.elem == 1 ? launch_t<uint8_t, kNarrowRm>(v, kp, s, blocks, units_x, units, uh)
                      : launch_t<uint16_t, kNarrowRm>(v, kp, s, blocks, units_x, units, uh);

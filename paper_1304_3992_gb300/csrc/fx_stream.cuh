@@ -52,12 +52,13 @@
 namespace fx {
 
 // Strip classes, by the largest sum of median radii r they serve: compact
-// (r <= 1: no median or one window-3 median), narrow (r <= 3) and wide
-// (r <= 7).  A 64-column window has 3 + r halo columns on each side (2 LoG +
-// 1 crossing + r median), 2 more when the standard deviation is taken over the
-// crossing map (its 5x5 window), so a strip has 58 - 2r output columns: 56, 52
-// or 44 (52, 48 or 40 for the crossing-map source).
-constexpr int kCompactRm = 1, kNarrowRm = 3, kWideRm = 7;
+// (r <= 1: no median or one window-3 median), narrow (r <= 3), wide (r <= 7)
+// and extra wide (r <= 11, e.g. 7, 7, 7).  A 64-column window has 3 + r halo
+// columns on each side (2 LoG + 1 crossing + r median), 2 more when the
+// standard deviation is taken over the crossing map (its 5x5 window), so a
+// strip has 58 - 2r output columns: 56, 52, 44 or 36 (52, 48, 40 or 32 for
+// the crossing-map source).
+constexpr int kCompactRm = 1, kNarrowRm = 3, kWideRm = 7, kXWideRm = 11;
 constexpr int strip_width(bool src_z, int rm_class) { return 58 - 2 * rm_class - (src_z ? 4 : 0); }
 constexpr int kDefaultUnitH = 512;
 // unit heights the batched plan's autotuner times
@@ -343,9 +344,10 @@ struct Ar<kModeF32LogWide> : Ar<kModeF32> {
 // kSd2: the branches have different standard-deviation thresholds (two S words).
 // kSrcZ: the standard deviation is taken over each branch's crossing map
 // (reading R4, source 1) from bit-sliced counts, at block level.
-// kRm: the strip class (kCompactRm, kNarrowRm or kWideRm): the halo, and for
-// the wide class the ring prefill one iteration earlier, so that the rows
-// above the unit that the outputs depend on are computed.
+// kRm: the strip class (kCompactRm, kNarrowRm, kWideRm or kXWideRm): the
+// halo, and for the wide classes the ring prefill one (two) iterations
+// earlier, so that the rows above the unit that the outputs depend on are
+// computed (the mask rows down to r above the unit).
 // Cst: RuntimeConsts, or the constants of a run-time compiled kernel (FP32
 // modes only).
 template <typename T, int kMode, bool kPair, bool kSd2, bool kSrcZ, int kRm = kNarrowRm, class Cst = RuntimeConsts>
@@ -355,7 +357,11 @@ struct Strip {
   // output columns: 2 LoG + 1 crossing (+ 2 standard deviation) + kRm median
   static constexpr int kLeftHalo = 3 + kRm + (kSrcZ ? 2 : 0), kOutCols = strip_width(kSrcZ, kRm);
   static_assert(2 * kLeftHalo + kOutCols == 64 && kLeftHalo % 2 == 0, "symmetric, even halo");
-  static constexpr int kK0 = kRm > kNarrowRm ? -3 : -2;  // first iteration (rows 4 kK0 .. are the ring prefill)
+  // first iteration (rows 4 kK0 .. are the ring prefill): the mask is valid
+  // from 3 rows below the first prefill row, so down to 4 |kK0| - 3 rows above
+  // the unit (block -1, from 19 rows above, holds them)
+  static constexpr int kK0 = kRm > kWideRm ? -4 : kRm > kNarrowRm ? -3 : -2;
+  static_assert(4 * -kK0 - 3 >= kRm, "the prefill reaches the rows the medians need");
   using V = typename A::V;
   using P = typename A::P;
   using Q = typename A::Q;

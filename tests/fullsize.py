@@ -20,7 +20,7 @@ def strip_width(r_m: int, source: int = 0) -> int:
     """Output columns of the streaming strip class serving median radius sum
     r_m: 64 minus twice the halo (3 + the class radius 1, 3 or 7, plus 2 for
     the crossing-map source)."""
-    rc = 1 if r_m <= 1 else 3 if r_m <= 3 else 7
+    rc = 1 if r_m <= 1 else 3 if r_m <= 3 else 7 if r_m <= 7 else 11
     return 58 - 2 * rc - (4 if source == 1 else 0)
 
 

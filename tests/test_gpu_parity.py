@@ -340,7 +340,8 @@ def test_batch_matches_single_and_oracle(cuda_lib):
         assert_same(singles[i], oracle.extract(np.ascontiguousarray(batch[i][0]), d8), f"oracle image {i}")
 
 
-@pytest.mark.parametrize("hmf,uw", [((5,), 52), ((3,), 56), ((7, 5, 3), 44), ((5, 5), 44), ((), 56)])
+@pytest.mark.parametrize("hmf,uw", [((5,), 52), ((3,), 56), ((7, 5, 3), 44), ((5, 5), 44), ((), 56),
+                                    ((7, 7, 7), 36)])
 def test_batch_full_range_16bit_all_groups(cuda_lib, hmf, uw):
     """All four queue groups (uint16 / uint8, aligned pairs / pixel by pixel)
     in one batch, the uint16 images spanning the full 16-bit range: their
@@ -441,13 +442,14 @@ def test_device_pointer_checks(cuda_lib):
 
 
 @pytest.mark.parametrize("hmf", [(5, 3), (3, 5), (3, 3), (7,), (3, 3, 3), (5, 5), (7, 5, 3), (7, 7),
-                                 (5, 3, 3, 3), (3, 3, 3, 3), (7, 7, 7)])
+                                 (5, 3, 3, 3), (3, 3, 3, 3), (7, 7, 7), (7, 7, 5, 3), (7, 7, 7, 7)])
 def test_median_lists_streaming(cuda_lib, hmf):
     """Median lists (Sec. 3.4 windows 3, 5, 7; Sec. 4.2's repeated passes):
-    radii adding up to 3 run on the narrow streaming strips, 4 to 7 on the wide
-    ones (7, 7, 7 on the general tile kernel); full masks of images taller than
-    one work unit, both dtypes, against the oracle, and the batched plan (narrow
-    strips or the general kernel) against single calls."""
+    radii adding up to 1 run on the compact streaming strips, 2 and 3 on the
+    narrow ones, 4 to 7 on the wide ones, 8 to 11 on the extra-wide ones
+    (7, 7, 7 and 7, 7, 5, 3) and 7, 7, 7, 7 (radius 12) on the general tile
+    kernel; full masks of images taller than one work unit, both dtypes,
+    against the oracle, and the batched plan against single calls."""
     imgs = [scenes.scene(700, 1100, seed=61, n_rects=300, noise_sigma=24.0, impulse_frac=0.01, bits=12),
             scenes.scene(1030, 613, seed=62, n_rects=250, noise_sigma=4.0, impulse_frac=0.01, bits=8)]
     d, p = pair(16.0, hmf=hmf)
@@ -546,11 +548,12 @@ def test_tiny_images_hand_cases_gpu(cuda_lib, hmf):
         assert run(cuda_lib, row, p).nonzero()[1].tolist() == [20 if b > a else 19]
 
 
-@pytest.mark.parametrize("hmf", [(7,), (5, 5), (7, 5, 3)])
-@pytest.mark.parametrize("shape", [(1, 1), (2, 45), (45, 2), (31, 44), (97, 89), (203, 157), (77, 133)])
+@pytest.mark.parametrize("hmf", [(7,), (5, 5), (7, 5, 3), (7, 7, 7), (7, 7, 7, 5)])
+@pytest.mark.parametrize("shape", [(1, 1), (2, 45), (45, 2), (31, 44), (97, 89), (203, 157), (77, 133), (50, 37)])
 def test_ragged_sizes_window7_and_wide(cuda_lib, shape, hmf):
-    """Window 7 and wide median lists on ragged sizes (widths around the 44- and
-    52-column strips, single rows and columns) against the oracle."""
+    """Window 7 and wide median lists on ragged sizes (widths around the 44-,
+    36- and 52-column strips, single rows and columns) against the oracle;
+    7, 7, 7 and 7, 7, 7, 5 (radii 9 and 11) run on the extra-wide strips."""
     h, w = shape
     img = scenes.scene(w, h, seed=h * 7 + w, n_rects=max(1, h * w // 300), noise_sigma=24.0,
                        impulse_frac=0.01, bits=12)

@@ -98,7 +98,7 @@ def test_specialize_argument_checks(fx):
     assert lib.fx_specialize(ctypes.byref(q), fx.FX_U16) == 1
     big = fx.make_params(fx.FX_U16, 16, mask_q=1 << 19)
     assert lib.fx_specialize(ctypes.byref(big), fx.FX_U16) == 3
-    assert lib.fx_specialize(ctypes.byref(fx.make_params(fx.FX_U16, 12, hmf=(7, 7, 7))), fx.FX_U16) == 2
+    assert lib.fx_specialize(ctypes.byref(fx.make_params(fx.FX_U16, 12, hmf=(7, 7, 7, 7))), fx.FX_U16) == 2
 
 
 def test_plan_argument_checks(fx):

@@ -33,6 +33,7 @@ CASES = [
     ("median 3 (compact strips)", dict(hmf=(3,))),
     ("no median (compact strips)", dict(hmf=())),
     ("median 7, 5, 3 (wide strips)", dict(hmf=(7, 5, 3))),
+    ("median 7, 7, 7 (extra-wide strips)", dict(hmf=(7, 7, 7))),
     ("branch thresholds differ", dict(t_sd5=(5.0, 7.0), t_sd3=(4.0, 6.0), t_sdmax=(20.0, 30.0))),
     ("crossing-map deviation", dict(stddev_source=1, t_sd5=(0.2, 0.3), t_sdmax=(0.45, 0.5), t_sd3=(0.3, 0.4))),
     ("other masks", dict(sigma=(0.8, 3.0), t_zc=(900.0, 400.0))),
@@ -103,10 +104,10 @@ def test_specialize_rejects_bad_arguments(cuda_lib):
     with pytest.raises(RuntimeError):
         fx.specialize(p, 7)
     # lists beyond the streaming kernel's radii (the general kernel) are not specialised
-    assert not fx.specialize(fx.make_params(fx.FX_U16, 12, hmf=(7, 7, 7)), fx.FX_U16)
+    assert not fx.specialize(fx.make_params(fx.FX_U16, 12, hmf=(7, 7, 7, 7)), fx.FX_U16)
 
 
-@pytest.mark.parametrize("hmf", [(5,), (3,), (7, 5, 3)])
+@pytest.mark.parametrize("hmf", [(5,), (3,), (7, 5, 3), (7, 7, 7)])
 def test_specialized_batched_path(cuda_lib, hmf):
     """Plans created after fx_specialize put the compiled group kernels in
     their graphs: uneven uint8 / uint16 scenes, the first three with
