@@ -521,7 +521,7 @@ def bench_variants(fx, torch, stream, band, out, band_np, reps=5):
                                "kernel": "streaming first pass (stops at the first block) + integer pass"}
     del wide
     med = torch.empty_like(band)
-    for w in (3, 5):
+    for w in (3, 5, 7):
         ms = timed(lambda: fx.hybrid_median(band, w, out=med, stream=stream))
         res[f"grayscale_median_{w}"] = {"gpx_s": px / ms / 1e6, "ms": ms, "kernel": "median tile",
                                         "gb_s": 4 * px / ms / 1e6}

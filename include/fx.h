@@ -273,7 +273,7 @@ fx_status fx_extract_host_batch(fx_plan *plan, const fx_image_desc *descs, int32
  * the image take the nearest image value.
  *   img, out     device pointers, same dtype; must not overlap
  *   pitch_bytes  input row pitch; out_pitch_bytes output row pitch (0 = packed)
- *   window       3 or 5
+ *   window       3, 5 or 7
  * Errors: FX_ERR_INVALID_ARG, FX_ERR_CUDA.  Allocates nothing.
  */
 fx_status fx_hybrid_median(const void *img, int64_t width, int64_t height, int64_t pitch_bytes,

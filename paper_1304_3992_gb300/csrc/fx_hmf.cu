@@ -2,21 +2,28 @@
 //
 // Output = median(median of the '+' subgroup, median of the 'x' subgroup,
 // centre), the subgroups being the centre row/column segment and the two
-// diagonals of the k x k window (2k - 1 values each, k = 3 or 5); pixels
+// diagonals of the k x k window (2k - 1 values each, k = 3, 5 or 7); pixels
 // outside the image take the value of the nearest image pixel (replicated
 // borders).  Medians come from exact min/max identities:
 //   med3(a, b, c)  = max(min(a, b), min(max(a, b), c))
 //   med5           = med3(c, max(min(a, b), min(d, e)), min(max(a, b), max(d, e)))
 //   med9 of three triples = med3(max of the triples' minima,
 //                                med3 of their medians, min of their maxima)
+// and, for the 13 values of a window-7 subgroup, forgetful selection: of any
+// m + 1 values of a set of 2m - 1, the smallest and the largest lie on either
+// side of the set's median, so dropping both keeps the median of the rest;
+// hold 8 values, drop the two ends, take in the next value, and repeat until
+// three values are left, whose median is the answer.  The ends are found by
+// compare-exchanges (min and max), which keep every other value.
 //
-// One warp walks down a strip of 60 output columns (a 64-column window with
-// one halo lane on each side), one input row per step.  Lane l holds the two
-// pixels of window columns 2l, 2l+1 as one u16x2 word, so every min/max
-// handles two pixels.  A ring of k rows keeps, per row, the words of the
-// lane's pixels shifted by -2..2 columns (neighbour lanes by shuffle, one-
-// column shifts by byte selection); loads are issued k rows ahead into a ring
-// of their own and never sit inside a branch.  For uint16 images read as
+// One warp walks down a strip of 60 output columns (56 for k = 7: a
+// 64-column window with one halo lane, two for k = 7, on each side), one
+// input row per step.  Lane l holds the two pixels of window columns 2l,
+// 2l+1 as one u16x2 word, so every min/max handles two pixels.  A ring of k
+// rows keeps, per row, the words of the lane's pixels shifted by -k/2..k/2
+// columns (neighbour lanes by shuffle, one-column shifts by byte selection);
+// loads are issued k rows ahead into a ring of their own and never sit inside
+// a branch.  For uint16 images read as
 // aligned pairs the loads go instead through a per-warp shared-memory ring of
 // kAsyncRows rows filled by cp.async, kAsyncRows - 1 rows ahead: many more
 // bytes in flight per SM than a register ring allows, at no register cost.
@@ -29,7 +36,6 @@
 namespace fx {
 namespace {
 
-constexpr int kHmfOut = 60;    // output columns per strip (lanes 1..30)
 constexpr int kHmfUnitH = 128; // output rows per strip unit
 constexpr int kHmfWarps = 4;   // warps per CTA
 constexpr int kAsyncRows = 16; // depth of the shared-memory load ring (power of two)
@@ -77,6 +83,38 @@ __device__ __forceinline__ uint32_t med9(uint32_t a0, uint32_t a1, uint32_t a2, 
   sort3(c0, c1, c2, cl, cm, ch);
   return med3(vmax(vmax(al, bl), cl), med3(am, bm, cm), vmin(vmin(ah, bh), ch));
 }
+// compare-exchange: a <- min, b <- max
+__device__ __forceinline__ void cx(uint32_t &a, uint32_t &b) {
+  const uint32_t lo = vmin(a, b);
+  b = vmax(a, b);
+  a = lo;
+}
+// the minimum of v[0..N-1] to v[0], the maximum to v[N-1], the other values
+// kept in v[1..N-2]: order each pair (0, 1), (2, 3), ..., then run the pairs'
+// smaller values (and an unpaired last one) through v[0] and their larger
+// values through v[N-1]
+template <int N>
+__device__ __forceinline__ void ends(uint32_t (&v)[8]) {
+#pragma unroll
+  for (int i = 0; i + 1 < N; i += 2) cx(v[i], v[i + 1]);
+#pragma unroll
+  for (int i = 2; i < N; i += 2) cx(v[0], v[i]);
+#pragma unroll
+  for (int i = 1; i < N - 1; i += 2) cx(v[i], v[N - 1]);
+}
+// median of 13 values by forgetful selection (v: the first 8, x: the other 5)
+__device__ __forceinline__ uint32_t med13(uint32_t (&v)[8], const uint32_t (&x)[5]) {
+  ends<8>(v);  // keep v[1..6]
+  v[0] = x[0];
+  ends<7>(v);  // keep v[1..5]
+  v[0] = x[1];
+  ends<6>(v);  // keep v[1..4]
+  v[0] = x[2];
+  ends<5>(v);  // keep v[1..3]
+  v[0] = x[3];
+  ends<4>(v);  // keep v[1..2]
+  return med3(v[1], v[2], x[4]);
+}
 
 // kPair: one aligned load of the lane's two pixels per row (base and pitch
 // multiples of two pixels, even width), the clamped columns picked by a byte
@@ -84,6 +122,8 @@ __device__ __forceinline__ uint32_t med9(uint32_t a0, uint32_t a1, uint32_t a2, 
 template <typename T, int K, bool kPair>
 struct HmfStrip {
   static constexpr int R = K / 2;
+  static constexpr int kHalo = (R + 1) / 2;     // halo lanes on each side
+  static constexpr int kOut = 64 - 4 * kHalo;   // output columns per strip
   static constexpr int L = K;  // loads run one window (k rows) ahead
   // aligned uint16 pairs: 4-byte asynchronous copies into the warp's ring
   static constexpr bool kAsync = kPair && sizeof(T) == 2;
@@ -104,14 +144,14 @@ struct HmfStrip {
   bool vst_;  // one store of the lane's two output pixels (aligned rows)
   bool colok_;  // FX_CHECKED: this lane's loaded columns lie in the image
   uint32_t raw0_[L], raw1_[L];  // loaded pixels of the next L rows
-  uint32_t win_[K][5];          // per ring row: the pair words shifted by -2..2 columns
+  uint32_t win_[K][K];          // per ring row: the pair words shifted by -R..R columns (index d + R)
 
   __device__ HmfStrip(const T *img, int64_t W_, int64_t H_, int64_t pitch_, T *out, int64_t opitch_, int64_t X0,
                       int64_t Y0_, int64_t Y1_)
       : pitch(pitch_), H(H_), Y0(Y0_), Y1(Y1_), W(W_), out_(reinterpret_cast<unsigned char *>(out)),
         opitch(opitch_) {
     lane = threadIdx.x & 31;
-    x = X0 - 2 + 2 * lane;
+    x = X0 - 2 * kHalo + 2 * lane;
     const int64_t c0 = x < 0 ? 0 : (x >= W ? W - 1 : x), c1 = x + 1 < 0 ? 0 : (x + 1 >= W ? W - 1 : x + 1);
     if constexpr (kPair) {
       const int64_t cb = (c0 < W - 2 ? c0 : W - 2) & ~int64_t{1};  // even pair holding both columns
@@ -183,29 +223,46 @@ struct HmfStrip {
     const uint32_t pv = __shfl_up_sync(kAll, w, 1), nx = __shfl_down_sync(kAll, w, 1);
     // refill the slot of row t - 1, whose value the previous step has used
     if constexpr (kAsync) issue(t + kAsyncRows - 1);
-    win_[S][0] = pv;                         // columns -2, -1
-    win_[S][1] = __byte_perm(pv, w, 0x5432); // -1, 0
-    win_[S][2] = w;
-    win_[S][3] = __byte_perm(w, nx, 0x5432); //  1, 2
-    win_[S][4] = nx;                         //  2, 3
+    uint32_t *row = win_[S];
+    if constexpr (R == 3) {
+      const uint32_t pv2 = __shfl_up_sync(kAll, w, 2), nx2 = __shfl_down_sync(kAll, w, 2);
+      row[0] = __byte_perm(pv2, pv, 0x5432);  // columns -3, -2
+      row[6] = __byte_perm(nx, nx2, 0x5432);  //  3, 4
+    }
+    if constexpr (R >= 2) {
+      row[R - 2] = pv;  // -2, -1
+      row[R + 2] = nx;  //  2, 3
+    }
+    row[R - 1] = __byte_perm(pv, w, 0x5432);  // -1, 0
+    row[R] = w;
+    row[R + 1] = __byte_perm(w, nx, 0x5432);  //  1, 2
     // centre row t - R of the window rows t - 2R .. t (ring slot (S + K - i) % K holds row t - i)
     const int32_t orow = t - 2 * R;  // output row relative to Y0
     if (orow < 0 || orow >= nrows_) return;
     constexpr int c = (S + K - R) % K;
     const uint32_t *C = win_[c];
     uint32_t h;
-    if constexpr (K == 5) {
+    if constexpr (K == 7) {
+      const uint32_t *N3 = win_[(S + 1) % K], *N2 = win_[(S + 2) % K], *N1 = win_[(S + 3) % K];
+      const uint32_t *S1 = win_[(S + 5) % K], *S2 = win_[(S + 6) % K], *S3 = win_[S];
+      // '+': the centre row segment and the column; 'x': both diagonals
+      uint32_t plus8[8] = {C[0], C[1], C[2], C[3], C[4], C[5], C[6], N3[3]};
+      const uint32_t plus5[5] = {N2[3], N1[3], S1[3], S2[3], S3[3]};
+      uint32_t cross8[8] = {N3[0], N2[1], N1[2], C[3], S1[4], S2[5], S3[6], N3[6]};
+      const uint32_t cross5[5] = {N2[5], N1[4], S1[2], S2[1], S3[0]};
+      h = med3(med13(plus8, plus5), med13(cross8, cross5), C[3]);
+    } else if constexpr (K == 5) {
       const uint32_t *N2 = win_[(S + 1) % K], *N1 = win_[(S + 2) % K], *S1 = win_[(S + 4) % K], *S2 = win_[S];
       const uint32_t plus = med9(C[0], C[1], C[2], C[3], C[4], N2[2], N1[2], S1[2], S2[2]);
       const uint32_t cross = med9(N2[0], N1[1], C[2], S1[3], S2[4], N2[4], N1[3], S1[1], S2[0]);
       h = med3(plus, cross, C[2]);
     } else {
       const uint32_t *N1 = win_[(S + 1) % K], *S1 = win_[S];
-      const uint32_t plus = med5(C[1], N1[2], C[2], S1[2], C[3]);
-      const uint32_t cross = med5(N1[1], N1[3], C[2], S1[1], S1[3]);
-      h = med3(plus, cross, C[2]);
+      const uint32_t plus = med5(C[0], N1[1], C[1], S1[1], C[2]);
+      const uint32_t cross = med5(N1[0], N1[2], C[1], S1[0], S1[2]);
+      h = med3(plus, cross, C[1]);
     }
-    if (lane < 1 || lane > 30 || x >= W) return;
+    if (lane < kHalo || lane > 31 - kHalo || x >= W) return;
     if (!FX_GUARD(x >= 0 && Y0 + orow < H)) return;
     unsigned char *d = outb_ + static_cast<uint64_t>(static_cast<uint32_t>(orow)) * opitch32_;
     if (vst_ && x + 1 < W) {  // x is even, so the pair is aligned
@@ -246,7 +303,7 @@ __global__ void __launch_bounds__(32 * kHmfWarps) hmf_stream_kernel(const T *img
   if (unit >= units) return;  // whole warps only
   const int64_t ux = unit % units_x, uy = unit / units_x;
   const int64_t Y0 = uy * kHmfUnitH, Y1 = Y0 + kHmfUnitH < H ? Y0 + kHmfUnitH : H;
-  HmfStrip<T, K, kPair> s(img, W, H, pitch, out, out_pitch, ux * kHmfOut, Y0, Y1);
+  HmfStrip<T, K, kPair> s(img, W, H, pitch, out, out_pitch, ux * HmfStrip<T, K, kPair>::kOut, Y0, Y1);
   if constexpr (HmfStrip<T, K, kPair>::kAsync) {
     __shared__ uint32_t ring[kHmfWarps][kAsyncRows][32];
     s.ring_ = ring[threadIdx.x >> 5];
@@ -257,14 +314,19 @@ __global__ void __launch_bounds__(32 * kHmfWarps) hmf_stream_kernel(const T *img
 template <typename T>
 cudaError_t launch_hmf(const T *img, int64_t W, int64_t H, int64_t pitch, T *out, int64_t opitch, int k,
                        cudaStream_t s) {
-  const int64_t units_x = (W + kHmfOut - 1) / kHmfOut, units = units_x * ((H + kHmfUnitH - 1) / kHmfUnitH);
+  const int64_t out_w = HmfStrip<T, 3, true>::kOut;  // the same for k = 3 and 5
+  const int64_t uw = k == 7 ? HmfStrip<T, 7, true>::kOut : out_w;
+  const int64_t units_x = (W + uw - 1) / uw, units = units_x * ((H + kHmfUnitH - 1) / kHmfUnitH);
   const int64_t blocks = (units + kHmfWarps - 1) / kHmfWarps;
   if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
   const unsigned g = static_cast<unsigned>(blocks);
   constexpr int nt = 32 * kHmfWarps;
   const int64_t two = 2 * static_cast<int64_t>(sizeof(T));
   const bool pair = reinterpret_cast<uintptr_t>(img) % two == 0 && pitch % two == 0 && W % 2 == 0;
-  if (k == 5) {
+  if (k == 7) {
+    if (pair) hmf_stream_kernel<T, 7, true><<<g, nt, 0, s>>>(img, W, H, pitch, out, opitch, units_x, units);
+    else hmf_stream_kernel<T, 7, false><<<g, nt, 0, s>>>(img, W, H, pitch, out, opitch, units_x, units);
+  } else if (k == 5) {
     if (pair) hmf_stream_kernel<T, 5, true><<<g, nt, 0, s>>>(img, W, H, pitch, out, opitch, units_x, units);
     else hmf_stream_kernel<T, 5, false><<<g, nt, 0, s>>>(img, W, H, pitch, out, opitch, units_x, units);
   } else {
@@ -283,7 +345,7 @@ extern "C" fx_status fx_hybrid_median(const void *img, int64_t width, int64_t he
                                       fx_dtype dtype, int32_t window, void *out, int64_t out_pitch_bytes,
                                       void *stream) {
   NvtxRange range("fx_hybrid_median");
-  if (window != 3 && window != 5) return FX_ERR_INVALID_ARG;
+  if (window != 3 && window != 5 && window != 7) return FX_ERR_INVALID_ARG;
   if (!img || !out || (dtype != FX_U8 && dtype != FX_U16)) return FX_ERR_INVALID_ARG;
   const int64_t elem = dtype == FX_U8 ? 1 : 2;
   if (out_pitch_bytes == 0) out_pitch_bytes = width * elem;
