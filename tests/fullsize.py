@@ -1,7 +1,7 @@
 """Row bands of the full-size parity tests.
 
 fx_extract splits an image into work units of uh output rows (a warp walks a
-strip of 56, 52 or 44 output columns over uh rows); a unit starts its rows with a prefill and ends
+strip of 56, 52, 44 or 36 output columns over uh rows); a unit starts its rows with a prefill and ends
 with the rows its outputs need, and its 16-row bit blocks restart at each
 unit.  The bands compared with the oracle therefore straddle unit seams on
 purpose.  unit_height() restates the launch's wave model (rows walked x waves
@@ -18,8 +18,8 @@ WARPS_PER_CTA = 1
 
 def strip_width(r_m: int, source: int = 0) -> int:
     """Output columns of the streaming strip class serving median radius sum
-    r_m: 64 minus twice the halo (3 + the class radius 1, 3 or 7, plus 2 for
-    the crossing-map source)."""
+    r_m: 64 minus twice the halo (3 + the class radius 1, 3, 7 or 11, plus 2
+    for the crossing-map source)."""
     rc = 1 if r_m <= 1 else 3 if r_m <= 3 else 7 if r_m <= 7 else 11
     return 58 - 2 * rc - (4 if source == 1 else 0)
 
