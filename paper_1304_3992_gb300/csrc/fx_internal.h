@@ -110,7 +110,6 @@ unsigned long long checked_count_noalloc(bool reset);
 unsigned long long checked_count_hmf(bool reset);
 bool checked_build();
 bool fast_path_supported(const KParams &kp);  // the streaming kernels (compact, narrow, wide or extra-wide strips)
-bool stream_narrow(const KParams &kp);        // the narrow strips serve it (also the batched kernels)
 int strip_class(const KParams &kp);           // the smallest strip class that serves kp (its median radius sum)
 cudaError_t launch_compact(const ImageView &v, const KParams &kp, cudaStream_t s, int64_t blocks, int64_t units_x,
                            int64_t units, int uh);

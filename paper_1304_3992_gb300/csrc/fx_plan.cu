@@ -84,7 +84,7 @@ struct fx_plan {
   KParams kp8, kp16;
   fx_status st16;  // FX_ERR_RANGE when 16-bit images cannot be evaluated exactly
   bool fast;
-  int rm_class;  // strip class of the streaming path (kCompactRm, kNarrowRm or kWideRm)
+  int rm_class;  // strip class of the streaming path (kCompactRm, kNarrowRm, kWideRm or kXWideRm)
   int device, max_images, num_sms;
   // batch workspace, double-buffered: graph i copies host table i into device
   // table i and runs on queue counters i, so two replays (e.g. from two
@@ -329,7 +329,7 @@ fx_status fx_plan_create(fx_plan **out, const fx_params *params, int32_t max_ima
   }
   p->st16 = make_kparams(params, 65535, &p->kp16);
   if (p->st16 != FX_OK) p->kp16 = p->kp8;
-  // the streaming path for median radii up to 7 (both parameter sets share the list)
+  // the streaming path for median radii up to 11 (both parameter sets share the list)
   p->fast = fast_path_supported(p->kp8) && fast_path_supported(p->kp16);
   p->rm_class = strip_class(p->kp8);
   p->device = device;

@@ -1,8 +1,9 @@
 // fx_plan_kernels.cuh -- the batched path's descriptor table and its
 // streaming group kernels for one strip class.  Included by fx_plan.cu
-// (narrow strips), fx_plan_compact.cu and fx_plan_wide.cu, so the classes
-// compile in parallel; the kernels have internal linkage and each class
-// exports its kernel selectors (fx_plan_kernels_of).
+// (narrow strips), fx_plan_compact.cu, fx_plan_wide.cu and fx_plan_xwide.cu,
+// so the classes compile in parallel; the kernels have internal linkage and
+// each class exports its kernel selectors (plan_fast_kernel_*,
+// plan_redo_kernel_*).
 #pragma once
 #ifndef __CUDACC_RTC__
 #include <cstdint>

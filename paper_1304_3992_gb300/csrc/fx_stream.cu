@@ -9,9 +9,8 @@ namespace fx {
 // The streaming kernels cover both standard-deviation sources and up to four
 // median passes: compact strips while the median radii add up to at most 1
 // (halo: 2 LoG + 1 crossing (+ 2 crossing-map deviation) + 1 median column),
-// narrow strips up to 3, wide strips up to 7, extra-wide strips up to 11.  The batched plans use the
-// narrow strips only.
-bool stream_narrow(const KParams &kp) { return kp.nhmf <= FX_MAX_HMF_LEVELS && kp.r_m <= kNarrowRm; }
+// narrow strips up to 3, wide strips up to 7, extra-wide strips up to 11.
+// The batched plans use the same classes (fx_plan.cu).
 bool fast_path_supported(const KParams &kp) { return kp.nhmf <= FX_MAX_HMF_LEVELS && kp.r_m <= kXWideRm; }
 int strip_class(const KParams &kp) {
   return kp.r_m <= kCompactRm ? kCompactRm : kp.r_m <= kNarrowRm ? kNarrowRm : kp.r_m <= kWideRm ? kWideRm : kXWideRm;

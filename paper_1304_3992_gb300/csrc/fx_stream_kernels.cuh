@@ -1,7 +1,8 @@
 // fx_stream_kernels.cuh -- the streaming kernels and their launch for one
-// strip class (compact: median radii up to 1; narrow: up to 3; wide: 4 .. 7).
-// Included by fx_stream_compact.cu, fx_stream.cu and fx_stream_wide.cu, so
-// the classes compile in parallel; every definition has internal linkage.
+// strip class (compact: median radii up to 1; narrow: up to 3; wide: 4 .. 7;
+// extra wide: 8 .. 11).  Included by fx_stream_compact.cu, fx_stream.cu,
+// fx_stream_wide.cu and fx_stream_xwide.cu, so the classes compile in
+// parallel; every definition has internal linkage.
 #pragma once
 #include <cstdint>
 
