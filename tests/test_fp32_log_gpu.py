@@ -165,16 +165,16 @@ def test_fp32_band16384_unit_seams_all_bands(cuda_lib):
             assert tolerance.compare_with_oracle(band, got[y0:y1], d, rows=(y0, y1)) == 0, f"band {b} rows {y0}:{y1}"
 
 
-def test_fp32_north_star_rule_literal(cuda_lib):
+def test_fp32_tiny_log_rule_literal(cuda_lib):
     """The FP32-LoG mode against the literal parity rule (differences only where
     the exact |LoG| is below 1e-5 of the local response range, at most 1e-6 of
     the pixels) and the zero-difference bar every FP32 test holds: the 512^2
     scene in full, sampled rows of the 8192^2 scene."""
     img = scenes.pan_512_u8()
     d, p = pair(1.0)
-    assert tolerance.compare_north_star(img, run(cuda_lib, img, p), d) == 0
+    assert tolerance.compare_tiny_log_rule(img, run(cuda_lib, img, p), d) == 0
     big = scenes.ms_8192_u16_11bit()
     d, p = pair(8.0)
     got = run(cuda_lib, big, p)
     for y0, y1 in _sample_rows(big.shape[0], 16, 4, 9):
-        assert tolerance.compare_north_star(big, got[y0:y1], d, rows=(y0, y1)) == 0
+        assert tolerance.compare_tiny_log_rule(big, got[y0:y1], d, rows=(y0, y1)) == 0

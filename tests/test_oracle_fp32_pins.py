@@ -216,7 +216,7 @@ def test_tolerance_excuses_only_near_fragile_sites():
         tolerance.check(got, exp, exc, cap=1.0)
 
 
-def test_north_star_rule_excuses_only_tiny_responses():
+def test_tiny_log_rule_excuses_only_tiny_responses():
     """The literal rule: a difference is excused only at a pixel whose exact
     |L| is below 1e-5 of the range of L over its 5x5 window, in either branch;
     the edge pixels of a step (|L| = 100 against a range of 200) are not."""
@@ -225,7 +225,7 @@ def test_north_star_rule_excuses_only_tiny_responses():
     L1[5, 3] = 1e-7
     L2 = np.full((20, 20), 7.0)
     L2[12, 12] = 0.0                   # an exact zero inside a flat patch: range 7, excused
-    exc = tolerance.north_star_excused([L1, L2])
+    exc = tolerance.tiny_log_excused([L1, L2])
     assert exc[5, 3] and exc[12, 12]
     assert not exc[5, 9] and not exc[5, 10] and not exc[0, 0]
     assert int(exc.sum()) == 2
@@ -238,14 +238,14 @@ def test_north_star_rule_excuses_only_tiny_responses():
         tolerance.check(got, exp, exc, cap=1.0)
 
 
-def test_north_star_rule_on_the_oracle_itself():
+def test_tiny_log_rule_on_the_oracle_itself():
     img = scenes.pan_512_u8()[:64, :96].copy()
     p = params()
     exp = oracle.extract(img, p)
-    assert tolerance.compare_north_star(img, exp.copy(), p) == 0
+    assert tolerance.compare_tiny_log_rule(img, exp.copy(), p) == 0
     bad = exp.copy()
     _, st = oracle.extract(img, p, stages=True)
-    ys, xs = np.nonzero(~tolerance.north_star_excused([st["L1"], st["L2"]]))
+    ys, xs = np.nonzero(~tolerance.tiny_log_excused([st["L1"], st["L2"]]))
     bad[ys[0], xs[0]] ^= 1
     with pytest.raises(AssertionError):
-        tolerance.compare_north_star(img, bad, p)
+        tolerance.compare_tiny_log_rule(img, bad, p)

@@ -97,7 +97,7 @@ def compare_with_oracle(img: np.ndarray, got_rows: np.ndarray, params: dict, row
     return check(got_rows, exp[sl], excused[sl])
 
 
-def north_star_excused(Ls, tau: float = TAU) -> np.ndarray:
+def tiny_log_excused(Ls, tau: float = TAU) -> np.ndarray:
     """The literal rule: pixels whose exact |L| (either branch) is below tau x
     the range of that branch's L over the 5x5 window at the pixel."""
     ex = np.zeros(Ls[0].shape, dtype=bool)
@@ -108,7 +108,7 @@ def north_star_excused(Ls, tau: float = TAU) -> np.ndarray:
     return ex
 
 
-def compare_north_star(img: np.ndarray, got_rows: np.ndarray, params: dict, rows=None) -> int:
+def compare_tiny_log_rule(img: np.ndarray, got_rows: np.ndarray, params: dict, rows=None) -> int:
     """The literal FP32 parity rule: differences only at pixels whose exact
     |LoG| is below 1e-5 of the local response range, at most 1e-6 of the
     pixels compared; returns the number of differences."""
@@ -116,7 +116,7 @@ def compare_north_star(img: np.ndarray, got_rows: np.ndarray, params: dict, rows
     y0, y1 = (0, H) if rows is None else rows
     a, b = max(0, y0 - 2), min(H, y1 + 2)
     exp, st = oracle.extract(img, params, rows=(a, b), stages=True)
-    excused = north_star_excused([st["L1"], st["L2"]])
+    excused = tiny_log_excused([st["L1"], st["L2"]])
     sl = slice(y0 - a, y1 - a)
     return check(got_rows, exp[sl], excused[sl])
 
