@@ -5,7 +5,7 @@ standard deviation, OR, hybrid median) over the 4 bands of a synthetic
 multispectral scene (12-bit values, band by band, one fused launch per band).
 Inputs are resident in HBM and larger than L2 (512 MiB per band).
 
-Prints one JSON line.  Keys beyond the driver contract:
+Prints one JSON line.  Beyond metric, value, unit, timing, clocks and e2e:
   roofline    the fused kernel against the measured HBM copy bandwidth
   issue_roof  the same kernel against the SM issue rate (lane-instructions)
   batched     64 uneven scenes (uint8/uint16 mixed) in one persistent
