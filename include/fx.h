@@ -192,9 +192,10 @@ typedef struct {
  * path and pixel type on the streaming path, then the redo pass), the batched
  * form of Sec. 6.2.2's one-thread-per-pixel mapping.  Median lists whose radii
  * add up to at most 11 run on the streaming strips of fx_extract (compact,
- * narrow, wide or extra wide), longer lists on the general tile kernel.  Each image's
- * mask is byte-identical to fx_extract's.  descs is a HOST array of n descriptors, validated like
- * fx_extract's arguments; the table is copied before the call returns.
+ * narrow, wide or extra wide), longer lists on the general tile kernel.
+ * Each image's mask is byte-identical to fx_extract's.  descs is a HOST array
+ * of n descriptors, validated like fx_extract's arguments; the table is
+ * copied before the call returns.
  * Output masks must not overlap each other or any input.
  * The plan holds two descriptor tables and two sets of queue counters and
  * alternates between them, so two calls on one plan may run at the same time
